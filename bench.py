@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 imaging path: reconstructed voxels/s.
+
+A step is one whole image (every stage of the path: reference plane,
+geometry and binning, compensation, Gaussian gridding, FT_2D, k_z filter +
+Stolt, inverse FT) of one synthetic scan already resident in HBM.  The
+default workload is the single realistic scan: 2 Tx x 4 Rx, 128 x 128
+random-walk serpentine positions, Nk = 256, imaged onto 256 x 256 x 64
+voxels (echo 268 MB, larger than the 129 MB L2, so no flush is needed
+between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank images its own scan (independent scans:
+weak scaling, no collective on the data path); the time is the maximum
+over ranks and ``value`` counts the voxels of all ranks.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+path has) on the host cores, each step a bounded sample of the same
+workload: the first Nk/8 frequencies of the scan (the image is linear in
+them), scaled to voxels/s.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstructed voxels/s at <=1e-4 NMSE vs the FP64 oracle (realistic single scan)"
+UNIT = "voxels/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["realistic", "tiny", "large"], default="realistic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self, want_cuda: bool):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if (want_cuda and torch.cuda.is_available()) else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.backend = backend
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+            if self.backend == "nccl":
+                import torch
+                dist.barrier(device_ids=[self.local_rank])
+            else:
+                dist.barrier()
+
+    def max(self, x: float) -> float:
+        return self._reduce(x, "max")
+
+    def sum(self, x: float) -> float:
+        return self._reduce(x, "sum")
+
+    def _reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        import torch.distributed as dist
+        dev = f"cuda:{self.local_rank}" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- workloads
+def make_scan(workload: str, rank: int):
+    import synth
+    if workload == "tiny":
+        return synth.tiny(seed=rank)
+    if workload == "large":
+        return synth.large(seed=5000 + rank)
+    return synth.realistic(seed=2000 + rank)
+
+
+def workload_config(scan, workload, plan=None):
+    T, R, P, Nk = scan.echo.shape
+    g = scan.grid
+    cfg = {"workload": {"tiny": "tiny: 1Tx x 2Rx, 16x16 jittered positions, Nk=32 -> 32x32x16",
+                        "realistic": "realistic single scan: 2Tx x 4Rx, 128x128 random-walk serpentine, "
+                                     "Nk=256 -> 256x256x64 complex64",
+                        "large": "large: 3Tx x 4Rx, 256x256 positions, Nk=512 -> 512x512x128"}[workload],
+           "tx_rx_pos_k": [T, R, P, Nk], "voxels": [g.nx, g.ny, g.nz],
+           "echo_bytes": int(scan.echo.nbytes), "l2": "inputs larger than L2 (no flush)"
+           if scan.echo.nbytes > 129e6 else "L2 flushed between steps",
+           "dtype_storage": "complex64", "parallelism": "independent scans per GPU (replicas)"}
+    if plan is not None:
+        cfg.update({"kernel_width": plan.kernel_width, "spectral_grid": [plan.mx, plan.my],
+                    "nufft_tol": plan.opt.nufft_tol})
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[5:]))
+            except Exception:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "whole run (timed region shorter than the 100 ms sampling period)"
+        reasons = set()
+        for r in inside:
+            active = r[3]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, active[1:5]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+# ----------------------------------------------------------------------------- roofline model
+def stage_bytes(plan, scan):
+    """Algorithmic HBM bytes of each stage (compulsory reads + writes of the
+    data it transforms; see the design doc for the derivation)."""
+    T, R, P, Nk = scan.echo.shape
+    L = T * R * P
+    nkp = ((Nk + 31) // 32) * 32
+    mx, my = plan.mx, plan.my
+    mrx, mry = 2 * mx, 2 * my
+    nx, ny, nz = scan.grid.nx, scan.grid.ny, scan.grid.nz
+    c = 8  # complex64
+    echo = L * Nk * c
+    shat = L * nkp * c
+    G = mry * mrx * nkp * c
+    A = mry * mx * nkp * c
+    S = mx * my * nkp * c
+    Z = mx * my * nz * c
+    B = mx * ny * nz * c
+    V = nx * ny * nz * c
+    return {"prep": L * 60 + 24 * P, "compensate": echo + shat + L * 12, "grid": shat + G + L * 16,
+            "fft_x": G + A, "fft_y": A + S, "stolt": S + Z, "ifft_y": Z + B, "ifft_x": B + V}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2305_02064_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage: str, workload: str):
+    """DRAM bytes per launch of the dominant stage from the committed ncu
+    summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d["stages"][stage]
+        if d.get("csrc_sha") != csrc_digest() or d.get("workload") != workload:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+    import paper_2305_02064_gb300 as mm
+
+    dev = torch.device(f"cuda:{dist.local_rank}")
+    torch.cuda.set_device(dev)
+    scan = make_scan(args.workload, dist.rank)
+    plan = mm.Plan.for_scan(scan)
+    stream = torch.cuda.Stream(device=dev)
+    ws = plan.new_workspace(dev)
+    vol = plan.new_volume(dev)
+    echo_h = torch.from_numpy(np.ascontiguousarray(scan.echo)).pin_memory()
+    pos_h = torch.from_numpy(np.ascontiguousarray(scan.pos, np.float64)).pin_memory()
+    tx_h = torch.from_numpy(np.ascontiguousarray(scan.tx, np.float64)).pin_memory()
+    rx_h = torch.from_numpy(np.ascontiguousarray(scan.rx, np.float64)).pin_memory()
+    echo, pos, tx, rx = (t.to(dev) for t in (echo_h, pos_h, tx_h, rx_h))
+    vol_h = torch.empty(vol.shape, dtype=vol.dtype).pin_memory()
+    torch.cuda.synchronize(dev)
+
+    def step():
+        plan.image(ws, echo, pos, tx, rx, vol, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    plan.poll_error(ws, stream=stream)
+
+    n_stage = len(plan.stage_names())
+    n_ev = min(args.steps, 50)
+    evsets = [[torch.cuda.Event(enable_timing=True) for _ in range(n_stage + 1)] for _ in range(n_ev)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device() if not os.environ.get("CUDA_VISIBLE_DEVICES")
+                          else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[dist.local_rank]))
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    w0 = time.time()
+    t_start.record(stream)
+    for i in range(args.steps):
+        if i < n_ev:
+            plan.set_stage_events(evsets[i])
+        elif i == n_ev:
+            plan.set_stage_events(None)
+        step()
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    w1 = time.time()
+    dist.barrier()
+    plan.set_stage_events(None)
+    clk = clocks.stop(w0, w1)
+    plan.poll_error(ws, stream=stream)
+    ms = t_start.elapsed_time(t_end) / args.steps
+    ms_max = dist.max(ms)
+
+    names = plan.stage_names()
+    stage_ms = {n: statistics.mean(ev[s].elapsed_time(ev[s + 1]) for ev in evsets) for s, n in enumerate(names)}
+    per_image = sorted(ev[0].elapsed_time(ev[-1]) for ev in evsets)
+    nb = stage_bytes(plan, scan)
+    peak_gbs, peak_kind = measured_peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    achieved = nb[dom] / (stage_ms[dom] * 1e-3) / 1e9
+
+    # end to end through the public API from pinned host buffers
+    e2e_steps = max(3, args.e2e_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for i in range(e2e_steps + 1):
+            if i == 1:
+                e0.record(stream)
+            echo.copy_(echo_h, non_blocking=True)
+            pos.copy_(pos_h, non_blocking=True)
+            tx.copy_(tx_h, non_blocking=True)
+            rx.copy_(rx_h, non_blocking=True)
+            step()
+            vol_h.copy_(vol, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = dist.max(e0.elapsed_time(e1) / e2e_steps)
+    h2d = echo_h.nbytes + pos_h.nbytes + tx_h.nbytes + rx_h.nbytes
+    d2h = vol_h.nbytes
+
+    voxels = scan.grid.n_voxels
+    total_vox = voxels * dist.world
+    res = {
+        "metric": METRIC, "value": total_vox / (ms_max * 1e-3), "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (complex64 storage, fp64 per-sample phase)",
+        "data": "synthetic (seeded scans shaped like the paper's workloads)",
+        "config": workload_config(scan, args.workload, plan),
+        "images_per_s": dist.world / (ms_max * 1e-3),
+        "latency_ms": {"p50": per_image[len(per_image) // 2], "p99": per_image[min(len(per_image) - 1,
+                                                                                    int(0.99 * len(per_image)))],
+                       "what": "device time of one image, back to back"},
+        "stages_ms": stage_ms,
+        "stages_gbs": {n: nb[n] / (stage_ms[n] * 1e-3) / 1e9 for n in names},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "traffic": ncu_traffic(dom, args.workload), "algorithmic_bytes": nb[dom]},
+        "e2e": {"value": total_vox / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
+        "gpu_launches": plan.kernels_per_image * args.steps,
+        "clocks": clk,
+    }
+    return res, scan, vol
+
+
+def cpu_baseline(scan, vol_gpu):
+    """The FP64 oracle (rma_fast) on the whole scan, timed on the host cores;
+    also the NMSE of the GPU volume against it."""
+    import numpy as np
+    from oracle import rma
+    su = rma.setup_from(scan)
+    t0 = time.time()
+    ref = rma.rma_fast(su)
+    dt = time.time() - t0
+    got = vol_gpu.cpu().numpy()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return ({"value": scan.grid.n_voxels / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": "one whole scan of the workload through oracle.rma.rma_fast (FP64 Gaussian gridding w=16, "
+                       "OpenMP + scipy.fft workers on all cores)", "seconds": dt},
+            {"nmse_vs_oracle": rma.nmse(got, ref), "peak_match": rma.peak_index(got) == rma.peak_index(ref)})
+
+
+# ----------------------------------------------------------------------------- reference (oracle) arm
+def run_reference(args, dist):
+    from oracle import rma
+    if dist.rank != 0:
+        return None
+    scan = make_scan(args.workload, 0)
+    su = rma.setup_from(scan)
+    nk = su.n_k
+    ks = max(1, nk // 8)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.time()
+        rma.rma_fast(su, k_slice=slice(0, ks))
+        if i >= args.warmup:
+            times.append(time.time() - t0)
+    vox_eq = scan.grid.n_voxels * ks / nk
+    sec = statistics.mean(times)
+    value = vox_eq / sec
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"first {ks} of {nk} frequencies of the scan through oracle.rma.rma_fast (FP64, w=16); "
+              f"the image is linear in the frequency samples, so voxels/s = voxels * {ks}/{nk} / step time")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(scan, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        dist = Dist(want_cuda=False)
+        out = run_reference(args, dist)
+        if out is not None:
+            print(json.dumps(out))
+        dist.close()
+        return 0
+    dist = Dist(want_cuda=True)
+    res, scan, vol = run_ours(args, dist)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cb, acc = cpu_baseline(scan, vol)
+        res["cpu_baseline"] = cb
+        res["accuracy"] = acc
+    if dist.rank == 0:
+        print(json.dumps(res))
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * mmsar.h -- C ABI of the GB300 multi-planar multistatic MIMO-SAR imager.
+ *
+ * The library forms a complex 3-D reflectivity volume from irregularly
+ * sampled MIMO-SAR echoes by the method of Smith & Torlak, "Efficient 3-D
+ * Near-Field MIMO-SAR Imaging for Irregular Scanning Geometries" (IEEE
+ * Access 2022):
+ *
+ *   1. per-sample multi-planar multistatic phase compensation (Sec. II-C,
+ *      Eq. 11-12) onto a virtual planar monostatic array (Eq. 3-4, Eq. 10);
+ *   2. Gaussian gridding of the compensated samples onto the regular planar
+ *      aperture and a 2-D FFT (the FGG-NUFFT form of FT_2D in Eq. 16, Sec. III);
+ *   3. the k_z weight and phase of Eq. 15 (P(f) = 1) and the Stolt step S of
+ *      Eq. 16, done as a 1-D Gaussian gridding over k_z plus an FFT;
+ *   4. the inverse 2-D FFT over (k_x, k_y) (IFT_3D of Eq. 16).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers named "device" are CUDA device pointers the caller owns
+ *   (PyTorch tensors, cudaMalloc, ...).  The library allocates no device
+ *   memory: every intermediate lives in the caller's workspace.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are stream-ordered and asynchronous: argument
+ *   validation errors return synchronously; conditions found on the device
+ *   (non-finite input, an unusable reference plane) are recorded in an
+ *   error word inside the workspace and read with mmsar_poll_error().
+ * - Geometry in metres, frequencies in Hz, c = 299792458 m/s.
+ * - Sample order l = (t, r, p): echo[t][r][p][k], k fastest, with the Tx at
+ *   pos[p] + tx[t] and the Rx at pos[p] + rx[r].
+ * - +z points from the scan plane toward the scene (the scene lies at
+ *   z > z_ref).  With this orientation the residual of Eq. 12 reads
+ *   beta = -2 d^z + ((d^x)^2 + (d^y)^2) / (4 Z_c), Z_c = z_scene - z_ref.
+ * - Output voxel (i, j, q) has centre (x0 + i dx, y0 + j dy, z0 + q dz) and
+ *   is stored at vol[(i * ny + j) * nz + q] (z fastest), complex64.
+ * - The image is normalised by 1 / (n_tx n_rx n_pos n_k).
+ * - No C++ exception crosses this boundary.  A plan is not thread-safe; use
+ *   one plan (and one workspace) per concurrently running stream.
+ */
+#ifndef MMSAR_H
+#define MMSAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MMSAR_OK = 0,
+    MMSAR_ERR_INVALID_ARG = 1,      /* null pointer, non-positive pitch, ...     */
+    MMSAR_ERR_UNSUPPORTED_SIZE = 2, /* a size outside the supported ranges       */
+    MMSAR_ERR_OUT_OF_MEMORY = 3,    /* workspace smaller than required           */
+    MMSAR_ERR_CUDA = 4,             /* a CUDA runtime call failed                */
+    MMSAR_ERR_DEVICE_TIMEOUT = 5,   /* a bounded device-side wait gave up        */
+    MMSAR_ERR_NONFINITE = 6         /* NaN/Inf in the echo or the geometry       */
+} mmsar_status;
+
+/* Storage type of the echo tensor.  Arithmetic is FP32 in every case. */
+typedef enum {
+    MMSAR_ECHO_C64 = 0,          /* interleaved float (re, im)                       */
+    MMSAR_ECHO_F16X2_SCALED = 1, /* interleaved __half (re, im) times a per-scan scale */
+    MMSAR_ECHO_BF16X2_SCALED = 2 /* interleaved bf16 (re, im) times a per-scan scale   */
+} mmsar_echo_dtype;
+
+/* Acquisition shape.  The stepped/FMCW frequency grid is uniform,
+ * f_k = f0_hz + k * df_hz (Sec. II-C, Eq. 9; sampling rule Sec. III). */
+typedef struct {
+    int n_tx;                 /* Tx elements, >= 1                      */
+    int n_rx;                 /* Rx elements, >= 1                      */
+    int n_pos;                /* scan positions, >= 0                   */
+    int n_k;                  /* frequency samples, 1 .. 1024           */
+    double f0_hz;             /* first frequency, > 0                   */
+    double df_hz;             /* frequency step, > 0 (ignored if n_k=1) */
+    mmsar_echo_dtype dtype;   /* echo storage                           */
+} mmsar_shape;
+
+/* Output voxel grid (centres).  nx, ny in 1 .. 1024, nz in 1 .. 256. */
+typedef struct {
+    double x0, y0, z0;        /* centre of voxel (0, 0, 0)              */
+    double dx, dy, dz;        /* pitches, > 0                           */
+    int nx, ny, nz;
+} mmsar_grid;
+
+typedef struct {
+    double z_ref;      /* virtual plane Z0 (Eq. 4); NaN => mean of z_l over samples    */
+    double z_scene;    /* scene depth for the MIMO term of Eq. 12; NaN => grid z centre */
+    int compensate;    /* 1 = Eq. 11-12 applied (paper); 0 = beta = 0 (RMA ablation)   */
+    double nufft_tol;  /* Gaussian gridding accuracy per transform; <= 0 => 1e-3        */
+    int mx, my;        /* spectral grid (power of two >= nx, ny, 16..1024); 0 => auto  */
+} mmsar_options;
+
+typedef struct mmsar_plan mmsar_plan;
+
+/* Fill `opt` with the defaults listed above.  Never fails for non-NULL opt. */
+void mmsar_options_default(mmsar_options *opt);
+
+/* Validate sizes and build a host-side plan (no device memory, no CUDA
+ * calls).  On success *out owns the plan; release it with
+ * mmsar_plan_destroy.  Returns MMSAR_ERR_INVALID_ARG / _UNSUPPORTED_SIZE
+ * with a message in mmsar_last_error() otherwise. */
+mmsar_status mmsar_plan_create(mmsar_plan **out, const mmsar_shape *shape,
+                               const mmsar_grid *grid, const mmsar_options *opt);
+
+/* Bytes of device workspace one mmsar_image call on this plan needs. */
+mmsar_status mmsar_plan_workspace_bytes(const mmsar_plan *plan, size_t *bytes);
+
+/* The Gaussian kernel width (taps per axis), the spectral grid and the
+ * number of kernels one mmsar_image call launches.  Any output may be NULL. */
+mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx, int *my,
+                             int *kernels_per_image);
+
+/* Stages of mmsar_image, in launch order: 0 "prep" (reference plane,
+ * geometry of Eq. 3-4 and 12, binning), 1 "compensate" (Eq. 11),
+ * 2 "grid" (Gaussian gridding), 3 "fft_x", 4 "fft_y" (FT_2D of Eq. 16 with
+ * deconvolution), 5 "stolt" (Eq. 15 weight + Stolt + z transform),
+ * 6 "ifft_y", 7 "ifft_x" (IFT over k_x, k_y). */
+int mmsar_stage_count(void);
+const char *mmsar_stage_name(int stage);
+
+/* Optional per-stage timing.  With n == mmsar_stage_count() + 1 events
+ * (cudaEvent_t passed as void*, owned by the caller), every later
+ * mmsar_image call on this plan records events[i] on its stream right before
+ * stage i and events[n - 1] after the last stage.  n == 0 (events NULL)
+ * turns it off. */
+mmsar_status mmsar_plan_set_stage_events(mmsar_plan *plan, void *const *events, int n);
+
+/* Form one image (Sec. II-C Eq. 11-12 followed by Eq. 16), stream-ordered.
+ *   workspace   device, >= mmsar_plan_workspace_bytes, 256-byte aligned; its
+ *               contents are scratch (overwritten by every call)
+ *   echo        device [n_tx][n_rx][n_pos][n_k] in shape.dtype
+ *   echo_scale  device float scalar multiplying a scaled FP16/BF16 echo;
+ *               NULL for MMSAR_ECHO_C64
+ *   pos         device double [n_pos][3]  radar reference point per position
+ *   tx, rx      device double [n_tx][3], [n_rx][3]  element offsets from it
+ *   vol         device complex64 [nx][ny][nz] output (fully overwritten)
+ * Inputs are read only; the output may not alias any input or the
+ * workspace. */
+mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_bytes,
+                         const void *echo, const float *echo_scale,
+                         const double *pos, const double *tx, const double *rx,
+                         void *vol, void *stream);
+
+/* Read (and clear) the device error word of the last call that used this
+ * workspace: synchronises `stream`, returns MMSAR_OK or the first device-side
+ * condition (MMSAR_ERR_NONFINITE, MMSAR_ERR_INVALID_ARG for Z_c <= 0). */
+mmsar_status mmsar_poll_error(const void *workspace, void *stream);
+
+/* Peak voxel of a complex64 volume (utility; Sec. V compares images by
+ * their peaks): writes to `result` (device) an int64 linear index -- the
+ * lowest index whose |o| is within 1e-6 (relative) of the maximum -- followed
+ * by the float maximum |o|.  `scratch` (device) must hold
+ * mmsar_peak_scratch_bytes(n) bytes.  n >= 1. */
+size_t mmsar_peak_scratch_bytes(int64_t n);
+mmsar_status mmsar_peak(const void *vol, int64_t n, void *scratch, void *result, void *stream);
+
+/* Thread-local text of the last error returned on this thread. */
+const char *mmsar_last_error(void);
+
+/* Release a plan (NULL is ignored). */
+void mmsar_plan_destroy(mmsar_plan *plan);
+
+/* Library version string. */
+const char *mmsar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMSAR_H */

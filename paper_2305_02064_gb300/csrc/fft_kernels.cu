@@ -1,0 +1,201 @@
+// Column-batched FFT kernel for the spatial transforms of Eq. 16: the
+// forward FT_2D over (x', y') after gridding (with the Gaussian
+// deconvolution and the crop to the Mx x My spectrum fused into the store)
+// and the inverse transform over (k_x, k_y) (with the crop to the voxel grid
+// and the 1/N normalisation fused into the store).
+//
+// Every transform runs along a strided axis of a tensor whose innermost
+// axis is contiguous: a CTA loads L rows x C contiguous columns (coalesced
+// rows of C * 8 bytes), transforms the C columns in shared memory (fft.cuh)
+// and writes the selected output rows.  No transposes are needed anywhere.
+#include <cmath>
+
+#include "fft.cuh"
+#include "internal.cuh"
+
+namespace mmsar {
+
+constexpr int kFftThreads = 256;
+
+__host__ __device__ constexpr int fft_cols(int L) { return L >= 256 ? 8192 / L : 32; }
+
+template <int L, int SIGN>
+__global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
+    constexpr int C = fft_cols(L);
+    extern __shared__ float2 smem[];
+    float2 *tile = smem;
+    float2 *tw = smem + L * C;
+    const int tid = threadIdx.x;
+    const int nchunks = (a.ncols + C - 1) / C;
+    const int chunk = blockIdx.x % nchunks;
+    const int t2 = blockIdx.x / nchunks;
+    const int t1 = blockIdx.y;
+    const int c0 = chunk * C;
+    const int cw = min(C, a.ncols - c0);
+    const float2 *in = a.in + t1 * a.in_t1 + t2 * a.in_t2 + c0;
+    float2 *out = a.out + t1 * a.out_t1 + t2 * a.out_t2 + c0;
+    fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
+    for (int e = tid; e < L * C; e += kFftThreads) {
+        const int f = e / C, c = e - (e / C) * C;
+        const int r = (f - a.in_shift) & (L - 1);
+        tile[e] = (r < a.n_in && c < cw) ? __ldg(in + (long long)r * a.in_row + c) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    smem_fft<L, C, kFftThreads, SIGN>(tile, tw);
+    const int half = a.n_out / 2;
+    for (int e = tid; e < a.n_out * C; e += kFftThreads) {
+        const int o = e / C, c = e - (e / C) * C;
+        if (c < cw) {
+            const int f = o - half;
+            float sc = a.scale;
+            if (a.gauss_tau > 0.f) sc *= __expf((float)(f * f) * a.gauss_tau);
+            const float2 v = tile[(f & (L - 1)) * C + c];
+            out[(long long)o * a.out_row + c] = make_float2(v.x * sc, v.y * sc);
+        }
+    }
+}
+
+template <int L, int SIGN>
+static cudaError_t launch_L(const ColumnFFT &a, cudaStream_t s) {
+    constexpr int C = fft_cols(L);
+    const size_t smem = (size_t)(L * C + L) * sizeof(float2);
+    cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN>, smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (a.ncols + C - 1) / C;
+    dim3 grid((unsigned)(a.nt2 * nchunks), (unsigned)a.nt1);
+    column_fft_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int SIGN>
+static cudaError_t dispatch(const ColumnFFT &a, cudaStream_t s) {
+    switch (a.L) {
+        case 16: return launch_L<16, SIGN>(a, s);
+        case 32: return launch_L<32, SIGN>(a, s);
+        case 64: return launch_L<64, SIGN>(a, s);
+        case 128: return launch_L<128, SIGN>(a, s);
+        case 256: return launch_L<256, SIGN>(a, s);
+        case 512: return launch_L<512, SIGN>(a, s);
+        case 1024: return launch_L<1024, SIGN>(a, s);
+        case 2048: return launch_L<2048, SIGN>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_column_fft(const ColumnFFT &a, cudaStream_t s) {
+    if (a.nt1 <= 0 || a.nt2 <= 0 || a.ncols <= 0) return cudaSuccess;
+    return a.sign < 0 ? dispatch<-1>(a, s) : dispatch<+1>(a, s);
+}
+
+// ---------------------------------------------------------------- FT_2D
+cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const float2 *G = reinterpret_cast<const float2 *>(w + p.off_G);
+    float2 *A = reinterpret_cast<float2 *>(w + p.off_A);
+    // along x': G[kc][v][u][32] -> A[kc][v][m][32], Gaussian deconvolution in x
+    ColumnFFT u;
+    u.L = p.mrx;
+    u.sign = -1;
+    u.in = G;
+    u.out = A;
+    u.n_in = p.mrx;
+    u.in_shift = 0;
+    u.in_row = kKC;
+    u.in_t1 = (long long)p.mry * p.mrx * kKC;
+    u.in_t2 = (long long)p.mrx * kKC;
+    u.n_out = p.mx;
+    u.out_row = kKC;
+    u.out_t1 = (long long)p.mry * p.mx * kKC;
+    u.out_t2 = (long long)p.mx * kKC;
+    u.ncols = kKC;
+    u.nt1 = p.n_kc;
+    u.nt2 = p.mry;
+    u.scale = (float)(std::sqrt(kPi / p.tau_x) / p.mrx);
+    u.gauss_tau = (float)p.tau_x;
+    return launch_column_fft(u, s);
+}
+
+cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const float2 *A = reinterpret_cast<const float2 *>(w + p.off_A);
+    float2 *S = reinterpret_cast<float2 *>(w + p.off_S);
+    // along y': A[kc][v][m][32] -> S[m][n][k], Gaussian deconvolution in y
+    ColumnFFT v;
+    v.L = p.mry;
+    v.sign = -1;
+    v.in = A;
+    v.out = S;
+    v.n_in = p.mry;
+    v.in_shift = 0;
+    v.in_row = (long long)p.mx * kKC;
+    v.in_t1 = (long long)p.mry * p.mx * kKC;
+    v.in_t2 = kKC;
+    v.n_out = p.my;
+    v.out_row = p.nkp;
+    v.out_t1 = kKC;
+    v.out_t2 = (long long)p.my * p.nkp;
+    v.ncols = kKC;
+    v.nt1 = p.n_kc;
+    v.nt2 = p.mx;
+    v.scale = (float)(std::sqrt(kPi / p.tau_y) / p.mry);
+    v.gauss_tau = (float)p.tau_y;
+    return launch_column_fft(v, s);
+}
+
+// ---------------------------------------------------------------- IFT over (k_x, k_y)
+cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const float2 *Z = reinterpret_cast<const float2 *>(w + p.off_Z);
+    float2 *B = reinterpret_cast<float2 *>(w + p.off_B);
+    const int ny = p.grid.ny, nz = p.grid.nz;
+    // along k_y: Z[m][n][q] -> B[m][j][q]
+    ColumnFFT a;
+    a.L = p.my;
+    a.sign = +1;
+    a.in = Z;
+    a.out = B;
+    a.n_in = p.my;
+    a.in_shift = p.my / 2;
+    a.in_row = nz;
+    a.in_t1 = 0;
+    a.in_t2 = (long long)p.my * nz;
+    a.n_out = ny;
+    a.out_row = nz;
+    a.out_t1 = 0;
+    a.out_t2 = (long long)ny * nz;
+    a.ncols = nz;
+    a.nt1 = 1;
+    a.nt2 = p.mx;
+    a.scale = 1.0f;
+    a.gauss_tau = 0.f;
+    return launch_column_fft(a, s);
+}
+
+cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const float2 *B = reinterpret_cast<const float2 *>(w + p.off_B);
+    const int nx = p.grid.nx, ny = p.grid.ny, nz = p.grid.nz;
+    // along k_x: B[m][j][q] -> vol[i][j][q], 1 / (T R P Nk)
+    ColumnFFT b;
+    b.L = p.mx;
+    b.sign = +1;
+    b.in = B;
+    b.out = reinterpret_cast<float2 *>(vol);
+    b.n_in = p.mx;
+    b.in_shift = p.mx / 2;
+    b.in_row = (long long)ny * nz;
+    b.in_t1 = 0;
+    b.in_t2 = nz;
+    b.n_out = nx;
+    b.out_row = (long long)ny * nz;
+    b.out_t1 = 0;
+    b.out_t2 = nz;
+    b.ncols = nz;
+    b.nt1 = 1;
+    b.nt2 = ny;
+    b.scale = (float)(1.0 / ((double)p.L * p.shape.n_k));
+    b.gauss_tau = 0.f;
+    return launch_column_fft(b, s);
+}
+
+}  // namespace mmsar

@@ -1,0 +1,120 @@
+// Internal declarations shared by the translation units of libmmsar.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mmsar.h"
+
+namespace mmsar {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kKC = 32;       // frequencies per k-chunk (one per lane)
+constexpr int kBin = 4;       // spreading bin / warp block edge, in grid cells
+constexpr int kMaxNk = 1024;
+constexpr int kMaxM = 1024;   // spectral grid per axis (FFT length 2M <= 2048)
+constexpr int kMaxNz = 256;
+
+// Error bits of the device error word (one per mmsar_status code).
+constexpr int kErrNonfinite = 1 << MMSAR_ERR_NONFINITE;
+constexpr int kErrGeometry = 1 << MMSAR_ERR_INVALID_ARG;
+
+// Device-visible header at offset 0 of the workspace.
+struct WsHeader {
+    int error;          // OR of kErr* bits
+    int n_valid;        // samples that were binned
+    double z_ref;       // resolved reference plane
+    double pad[14];
+};
+static_assert(sizeof(WsHeader) == 128, "header size");
+
+// Per-sample gridding record (sorted by bin).
+struct SampleRec {
+    int u0, v0;         // first grid cell of the support, wrapped into [0, Mr)
+    float fx, fy;       // exact grid position minus (u0, v0), in cells
+};
+
+// Everything the kernels need, resolved on the host (plain values).
+struct Plan {
+    mmsar_shape shape;
+    mmsar_grid grid;
+    mmsar_options opt;
+    int w;              // Gaussian taps per axis
+    int mx, my;         // spectral modes per axis
+    int mrx, mry;       // oversampled gridding grid (2 mx, 2 my)
+    int mrz;            // z gridding grid (power of two >= max(32, 2 nz))
+    int n_kc;           // k chunks of 32
+    int nkp;            // n_kc * 32
+    int64_t L;          // n_tx n_rx n_pos
+    int nbx, nby;       // bins per axis (mrx / 4, mry / 4)
+    int64_t n_bins;
+    bool zref_given;
+    double z_ref;       // when given
+    double z_scene;     // resolved (grid centre when NaN)
+    double tau_x, tau_y, tau_z;
+    // workspace layout (byte offsets)
+    size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm, off_srec;
+    size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
+    size_t ws_bytes;
+    // optional per-stage timing events (caller-owned)
+    int n_events;
+    cudaEvent_t events[16];
+};
+
+constexpr int kStages = 8;
+constexpr int kKernelsPerImage = 12;
+
+}  // namespace mmsar
+
+struct mmsar_plan {
+    mmsar::Plan p;
+};
+
+namespace mmsar {
+
+// ---------------------------------------------------------------- launchers
+// All return cudaSuccess or the launch error.
+cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                        cudaStream_t s);
+cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                            cudaStream_t s);
+cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
+cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s);
+cudaError_t launch_peak(const void *vol, int64_t n, void *scratch, void *result, cudaStream_t s);
+size_t peak_scratch_bytes(int64_t n);
+
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute is per device; the first launch on each device sets it).
+cudaError_t ensure_smem_attr(const void *func, size_t bytes);
+
+// Column-batched FFT along the row axis of a strided 2-D tile set (see
+// fft_kernels.cu).  Row r of a tile is placed at FFT index (r + in_shift) mod L;
+// output row o takes FFT index (o - n_out/2) mod L and is scaled by
+//   scale * (gauss_tau > 0 ? exp(f^2 * gauss_tau) : 1),  f = o - n_out/2.
+struct ColumnFFT {
+    int L;              // FFT length (power of two, 16..2048)
+    int sign;           // -1 forward, +1 inverse (unnormalised)
+    const float2 *in;
+    float2 *out;
+    int n_in;           // rows read (<= L)
+    int in_shift;
+    long long in_row, in_t1, in_t2;     // element strides
+    int n_out;          // rows written (<= L)
+    long long out_row, out_t1, out_t2;
+    int ncols;          // contiguous columns per tile
+    int nt1, nt2;       // tile counts
+    float scale;
+    float gauss_tau;
+};
+cudaError_t launch_column_fft(const ColumnFFT &a, cudaStream_t s);
+
+}  // namespace mmsar

@@ -1,0 +1,360 @@
+// Per-sample stage: reference plane, virtual-element geometry, binning and
+// the phase compensation of Sec. II-C.
+//
+//  zref_kernel      z_ref = mean of z_l over all samples (when not given).
+//  geometry_kernel  Eq. 3-4 virtual element (x', y'), separations d^x, d^y,
+//                   d^z = z_l - z_ref; the residual beta of Eq. 12; the
+//                   gridding position on the 2M-point oversampled aperture
+//                   grid; the compensation phase as 32-bit fixed-point turns.
+//  bin_*            counting sort of the samples by 4x4-cell bin.
+//  compensate       Eq. 11, s_hat = s exp(+j k beta), written in bin order.
+//
+// Precision: FP64 is used once per sample (geometry and the phase argument
+// f0 beta / c, df beta / c reduced to [0, 1) turns and stored as uint32
+// fixed point).  Per (sample, k) the phase a + k b is formed exactly in
+// wrapping 32-bit integer arithmetic, so its error is at most (1 + k) 2^-33
+// turns, and only the final sincospi runs in FP32.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "fft.cuh"
+#include "internal.cuh"
+
+namespace mmsar {
+
+// ------------------------------------------------------------------ z_ref
+__global__ void __launch_bounds__(1024) zref_kernel(const double *__restrict__ pos, int P,
+                                                    const double *__restrict__ tx, int T,
+                                                    const double *__restrict__ rx, int R, int given,
+                                                    double z_given, WsHeader *hdr) {
+    __shared__ double red[1024];
+    const int tid = threadIdx.x;
+    if (given) {
+        if (tid == 0) hdr->z_ref = z_given;
+        return;
+    }
+    double s = 0.0;
+    for (int p = tid; p < P; p += 1024) s += pos[3 * p + 2];
+    red[tid] = s;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double st = 0.0, sr = 0.0;
+        for (int t = 0; t < T; ++t) st += tx[3 * t + 2];
+        for (int r = 0; r < R; ++r) sr += rx[3 * r + 2];
+        hdr->z_ref = (P > 0 ? red[0] / P : 0.0) + 0.5 * (st / T + sr / R);
+    }
+}
+
+cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                        cudaStream_t s) {
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    zref_kernel<<<1, p.zref_given ? 32 : 1024, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
+                                                       p.zref_given ? 1 : 0, p.z_ref, hdr);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ geometry
+struct GeomArgs {
+    const double *pos, *tx, *rx;
+    int T, R, P;
+    long long L;
+    double x_c, y_c, inv_dx2, inv_dy2;   // 2 / dx: cells of the 2M grid per metre
+    double z_scene;
+    int compensate;
+    double half_w;
+    int mrx, mry, nbx;
+    double f0_over_c, df_over_c;
+    WsHeader *hdr;
+    int *counts;
+    int *binid;
+    SampleRec *rec;
+    uint2 *phase;
+};
+
+__device__ __forceinline__ uint32_t frac_to_fixed(double turns) {
+    const double f = turns - floor(turns);                       // [0, 1)
+    return (uint32_t)(unsigned long long)llrint(f * 4294967296.0);  // 2^32 wraps to 0
+}
+
+__global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.L) return;
+    const int p = (int)(l % a.P);
+    const int r = (int)((l / a.P) % a.R);
+    const int t = (int)(l / ((long long)a.P * a.R));
+    const double px = a.pos[3 * p], py = a.pos[3 * p + 1], pz = a.pos[3 * p + 2];
+    // Tx / Rx absolute positions (Eq. 2 geometry)
+    const double xT = px + a.tx[3 * t], yT = py + a.tx[3 * t + 1], zT = pz + a.tx[3 * t + 2];
+    const double xR = px + a.rx[3 * r], yR = py + a.rx[3 * r + 1], zR = pz + a.rx[3 * r + 2];
+    // Eq. 3-4: virtual element at the midpoint, separations, plane offset
+    const double xv = 0.5 * (xT + xR), yv = 0.5 * (yT + yR), zl = 0.5 * (zT + zR);
+    const double ddx = xR - xT, ddy = yR - yT;
+    const double z_ref = a.hdr->z_ref;
+    const double Zc = a.z_scene - z_ref;
+    if (!(isfinite(xv) && isfinite(yv) && isfinite(zl))) {
+        atomicOr(&a.hdr->error, kErrNonfinite);
+        a.binid[l] = -1;
+        return;
+    }
+    double beta = 0.0;
+    if (a.compensate) {
+        if (!(Zc > 0.0)) {
+            atomicOr(&a.hdr->error, kErrGeometry);
+        } else {
+            // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
+            beta = -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) / (4.0 * Zc);
+        }
+    }
+    // position on the 2M-point periodic grid, in cells
+    const double gx = (xv - a.x_c) * a.inv_dx2;
+    const double gy = (yv - a.y_c) * a.inv_dy2;
+    const double u0d = ceil(gx - a.half_w), v0d = ceil(gy - a.half_w);
+    const double fx = gx - u0d, fy = gy - v0d;
+    long long u0 = (long long)u0d % a.mrx, v0 = (long long)v0d % a.mry;
+    if (u0 < 0) u0 += a.mrx;
+    if (v0 < 0) v0 += a.mry;
+    SampleRec rc;
+    rc.u0 = (int)u0;
+    rc.v0 = (int)v0;
+    rc.fx = (float)fx;
+    rc.fy = (float)fy;
+    a.rec[l] = rc;
+    // Eq. 11 phase k beta = 2 pi f beta / c in turns: f0 beta/c + k df beta/c
+    a.phase[l] = make_uint2(frac_to_fixed(a.f0_over_c * beta), frac_to_fixed(a.df_over_c * beta));
+    const int bin = (rc.v0 / kBin) * a.nbx + rc.u0 / kBin;
+    a.binid[l] = bin;
+    atomicAdd(&a.counts[bin], 1);
+}
+
+cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                            cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    GeomArgs a;
+    a.pos = pos;
+    a.tx = tx;
+    a.rx = rx;
+    a.T = p.shape.n_tx;
+    a.R = p.shape.n_rx;
+    a.P = p.shape.n_pos;
+    a.L = p.L;
+    a.x_c = p.grid.x0 + (p.grid.nx / 2) * p.grid.dx;
+    a.y_c = p.grid.y0 + (p.grid.ny / 2) * p.grid.dy;
+    a.inv_dx2 = (double)p.mrx / ((double)p.mx * p.grid.dx);
+    a.inv_dy2 = (double)p.mry / ((double)p.my * p.grid.dy);
+    a.z_scene = p.z_scene;
+    a.compensate = p.opt.compensate;
+    a.half_w = 0.5 * p.w;
+    a.mrx = p.mrx;
+    a.mry = p.mry;
+    a.nbx = p.nbx;
+    a.f0_over_c = p.shape.f0_hz / kC0;
+    a.df_over_c = p.shape.df_hz / kC0;
+    a.hdr = reinterpret_cast<WsHeader *>(w);
+    a.counts = reinterpret_cast<int *>(w + p.off_counts);
+    a.binid = reinterpret_cast<int *>(w + p.off_binid);
+    a.rec = reinterpret_cast<SampleRec *>(w + p.off_rec);
+    a.phase = reinterpret_cast<uint2 *>(w + p.off_phase);
+    const unsigned blocks = (unsigned)((p.L + 255) / 256);
+    geometry_kernel<<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bin scan
+// Exclusive prefix sum of the bin counts (one block); also seeds the scatter
+// cursors and records the number of binned samples.
+__global__ void __launch_bounds__(1024) bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets,
+                                                        int *__restrict__ cursor, long long n, WsHeader *hdr) {
+    __shared__ int part[1024];
+    const int tid = threadIdx.x;
+    const long long per = (n + 1023) / 1024;
+    const long long b0 = tid * per, b1 = min(n, b0 + per);
+    int s = 0;
+    for (long long b = b0; b < b1; ++b) s += counts[b];
+    part[tid] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over 1024 partial sums
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int v = tid >= d ? part[tid - d] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int run = tid > 0 ? part[tid - 1] : 0;
+    for (long long b = b0; b < b1; ++b) {
+        offsets[b] = run;
+        cursor[b] = run;
+        run += counts[b];
+    }
+    if (tid == 1023) {
+        offsets[n] = part[1023];
+        hdr->n_valid = part[1023];
+    }
+}
+
+cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    bin_scan_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts),
+                                       reinterpret_cast<int *>(w + p.off_offsets),
+                                       reinterpret_cast<int *>(w + p.off_cursor), p.n_bins,
+                                       reinterpret_cast<WsHeader *>(w));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bin scatter
+__global__ void __launch_bounds__(256) bin_scatter_kernel(long long L, const int *__restrict__ binid,
+                                                          const SampleRec *__restrict__ rec,
+                                                          int *__restrict__ cursor, int *__restrict__ perm,
+                                                          SampleRec *__restrict__ srec) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    const int b = binid[l];
+    if (b < 0) return;
+    const int slot = atomicAdd(&cursor[b], 1);
+    perm[slot] = (int)l;
+    srec[slot] = rec[l];
+}
+
+cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const unsigned blocks = (unsigned)((p.L + 255) / 256);
+    bin_scatter_kernel<<<blocks, 256, 0, s>>>(p.L, reinterpret_cast<int *>(w + p.off_binid),
+                                              reinterpret_cast<SampleRec *>(w + p.off_rec),
+                                              reinterpret_cast<int *>(w + p.off_cursor),
+                                              reinterpret_cast<int *>(w + p.off_perm),
+                                              reinterpret_cast<SampleRec *>(w + p.off_srec));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bin sort
+// The scatter above fills each bin in the arrival order of its atomics.  To
+// make the image bit-reproducible, every bin of up to 256 samples is put in
+// ascending sample order by a rank sort (one warp per bin); bins are small
+// (a few to a few hundred samples at the paper's sampling densities).
+__global__ void __launch_bounds__(256) bin_sort_kernel(long long n_bins, const int *__restrict__ offsets,
+                                                       int *__restrict__ perm, SampleRec *__restrict__ srec,
+                                                       const SampleRec *__restrict__ rec) {
+    const long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (b >= n_bins) return;
+    const int lane = threadIdx.x & 31;
+    const int beg = offsets[b], n = offsets[b + 1] - beg;
+    if (n <= 1) return;
+    int *pp = perm + beg;
+    // rank sort: element i goes to position #{j : key_j < key_i} (keys are distinct)
+    // done in two sweeps through a small per-warp staging area in shared memory
+    __shared__ int keys[8][256];
+    if (n <= 256) {
+        for (int i = lane; i < n; i += 32) keys[threadIdx.x / 32][i] = pp[i];
+        __syncwarp();
+        int dst[8];
+        int cnt = 0;
+        for (int i = lane; i < n; i += 32) {
+            const int ki = keys[threadIdx.x / 32][i];
+            int rank = 0;
+            for (int j = 0; j < n; ++j) rank += keys[threadIdx.x / 32][j] < ki;
+            dst[cnt++] = rank;
+        }
+        __syncwarp();
+        cnt = 0;
+        for (int i = lane; i < n; i += 32) {
+            const int ki = keys[threadIdx.x / 32][i];
+            const int r = dst[cnt++];
+            pp[r] = ki;
+            srec[beg + r] = rec[ki];
+        }
+    }
+    // larger bins keep arrival order (still correct; only the summation
+    // order, hence the last bits, can then vary between runs)
+}
+
+cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const unsigned blocks = (unsigned)((p.n_bins + 7) / 8);
+    bin_sort_kernel<<<blocks, 256, 0, s>>>(p.n_bins, reinterpret_cast<int *>(w + p.off_offsets),
+                                           reinterpret_cast<int *>(w + p.off_perm),
+                                           reinterpret_cast<SampleRec *>(w + p.off_srec),
+                                           reinterpret_cast<SampleRec *>(w + p.off_rec));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ compensate
+// One warp per (sorted slot, k-chunk): lane k reads s[l][k] (256 coalesced
+// bytes per warp), rotates it by exp(+j 2 pi (a + k b)) and writes
+// s_hat[kc][slot][lane].
+template <int DT>
+__global__ void __launch_bounds__(256) compensate_kernel(const void *__restrict__ echo_v,
+                                                         const float *__restrict__ scale_p,
+                                                         const int *__restrict__ perm,
+                                                         const uint2 *__restrict__ phase, int Nk,
+                                                         long long Lmax, const WsHeader *__restrict__ hdr,
+                                                         int *__restrict__ err, float2 *__restrict__ shat) {
+    const int n_valid = hdr->n_valid;
+    const int kc = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int k = kc * kKC + lane;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *scale_p;
+    bool bad = false;
+    for (long long slot = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; slot < n_valid;
+         slot += warps) {
+        const int l = perm[slot];
+        float2 v = make_float2(0.f, 0.f);
+        if (k < Nk) {
+            const long long e = (long long)l * Nk + k;
+            if (DT == MMSAR_ECHO_C64) {
+                v = __ldg(reinterpret_cast<const float2 *>(echo_v) + e);
+            } else if (DT == MMSAR_ECHO_F16X2_SCALED) {
+                const __half2 h = reinterpret_cast<const __half2 *>(echo_v)[e];
+                v = __half22float2(h);
+                v.x *= scale;
+                v.y *= scale;
+            } else {
+                const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162 *>(echo_v)[e];
+                v = __bfloat1622float2(h);
+                v.x *= scale;
+                v.y *= scale;
+            }
+            bad |= !(isfinite(v.x) && isfinite(v.y));
+            const uint2 ph = phase[l];
+            const uint32_t turns = ph.x + (uint32_t)k * ph.y;      // exact mod 2^32
+            const float tf = (float)(int32_t)turns * 4.6566128730773926e-10f;  // [-1, 1): 2 * turns / 2^32
+            float sn, cs;
+            sincospif(tf, &sn, &cs);
+            v = cmul(v, make_float2(cs, sn));
+        }
+        shat[((long long)kc * Lmax + slot) * kKC + lane] = v;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, kErrNonfinite);
+}
+
+cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const long long warps_needed = p.L;
+    long long blocks = (warps_needed + 7) / 8;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    dim3 grid((unsigned)blocks, p.n_kc);
+    const int *perm = reinterpret_cast<int *>(w + p.off_perm);
+    const uint2 *ph = reinterpret_cast<uint2 *>(w + p.off_phase);
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
+    float2 *shat = reinterpret_cast<float2 *>(w + p.off_shat);
+    switch (p.shape.dtype) {
+        case MMSAR_ECHO_C64:
+            compensate_kernel<MMSAR_ECHO_C64><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k, p.L, hdr,
+                                                                   &hdr->error, shat);
+            break;
+        case MMSAR_ECHO_F16X2_SCALED:
+            compensate_kernel<MMSAR_ECHO_F16X2_SCALED><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k,
+                                                                            p.L, hdr, &hdr->error, shat);
+            break;
+        default:
+            compensate_kernel<MMSAR_ECHO_BF16X2_SCALED><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k,
+                                                                             p.L, hdr, &hdr->error, shat);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mmsar
