@@ -133,6 +133,10 @@ class Plan:
             _lib.check(self._lib.mmsar_plan_set_stage_events(self._h, None, 0))
             self._events = None
             return
+        import torch
+        for e in events:
+            if not e.cuda_event:       # torch creates the CUDA event on its first record
+                e.record(torch.cuda.current_stream())
         arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
         _lib.check(self._lib.mmsar_plan_set_stage_events(self._h, arr, len(events)))
         self._events = list(events)

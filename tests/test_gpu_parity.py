@@ -179,3 +179,23 @@ def test_realistic_full_size_against_fast_oracle(dev):
     truth = [scan.grid.centre_index(*p[:3]) for p in scan.scatterers]
     hits = sum(1 for (i, j, q) in truth if np.abs(got[i, j, q]) > 0.2 * np.abs(got).max())
     assert hits > 0.5 * len(truth)
+
+
+def test_stage_events_time_every_stage(dev, tiny_scan):
+    from paper_2305_02064_gb300 import Plan
+    plan = Plan.for_scan(tiny_scan)
+    names = plan.stage_names()
+    assert names[0] == "prep" and names[-1] == "ifft_x" and len(names) == 8
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+    plan.set_stage_events(evs)
+    ws, vol = plan.new_workspace(dev), plan.new_volume(dev)
+    args = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            for a in (tiny_scan.echo, tiny_scan.pos, tiny_scan.tx, tiny_scan.rx)]
+    plan.image(ws, *args, vol)
+    torch.cuda.synchronize()
+    parts = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(names))]
+    assert all(p >= 0 for p in parts)
+    assert sum(parts) == pytest.approx(evs[0].elapsed_time(evs[-1]), rel=1e-3, abs=1e-3)
+    plan.set_stage_events(None)
+    plan.image(ws, *args, vol)
+    plan.poll_error(ws)
