@@ -154,6 +154,24 @@ mmsar_status mmsar_poll_error(const void *workspace, void *stream);
 size_t mmsar_peak_scratch_bytes(int64_t n);
 mmsar_status mmsar_peak(const void *vol, int64_t n, void *scratch, void *result, void *stream);
 
+/* Imaging without a caller-provided workspace (the paper has no
+ * counterpart; this is a deployment convenience).  For callers that cannot
+ * allocate device memory while they run -- hard real-time acquisition loops
+ * that forbid blocking or failing allocations after start-up, plug-ins that
+ * only receive buffers from their host -- this call runs mmsar_image on a
+ * scratch area built into the library: a fixed device array of
+ * mmsar_static_workspace_bytes() bytes (32 MiB) that every GPU using the
+ * library holds until the process exits.  Arguments as for mmsar_image; the
+ * caller still passes inputs and the output.  Plans whose workspace exceeds
+ * the area are rejected with MMSAR_ERR_UNSUPPORTED_SIZE.  The first call on
+ * each device looks up the area's device address (make it before any stream
+ * capture).  All calls on a device share the area: calls that overlap on the
+ * GPU race on it, so serialise them.  No device memory is allocated. */
+size_t mmsar_static_workspace_bytes(void);
+mmsar_status mmsar_image_static(mmsar_plan *plan, const void *echo, const float *echo_scale,
+                                const double *pos, const double *tx, const double *rx,
+                                void *vol, void *stream);
+
 /* Thread-local text of the last error returned on this thread. */
 const char *mmsar_last_error(void);
 

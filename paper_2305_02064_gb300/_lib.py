@@ -26,7 +26,7 @@ DTYPES = {"c64": 0, "f16": 1, "bf16": 2}
 EXPORTS = ["mmsar_options_default", "mmsar_plan_create", "mmsar_plan_workspace_bytes", "mmsar_plan_info",
            "mmsar_stage_count", "mmsar_stage_name", "mmsar_plan_set_stage_events",
            "mmsar_image", "mmsar_poll_error", "mmsar_peak_scratch_bytes", "mmsar_peak", "mmsar_last_error",
-           "mmsar_plan_destroy", "mmsar_version"]
+           "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static"]
 
 
 class MmsarError(RuntimeError):
@@ -96,6 +96,10 @@ def load(build_if_missing: bool = True):
         lib.mmsar_last_error.restype = ctypes.c_char_p
         lib.mmsar_plan_destroy.argtypes = [vp]
         lib.mmsar_plan_destroy.restype = None
+        lib.mmsar_static_workspace_bytes.argtypes = []
+        lib.mmsar_static_workspace_bytes.restype = sz
+        lib.mmsar_image_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.mmsar_image_static.restype = ctypes.c_int
         lib.mmsar_version.argtypes = []
         lib.mmsar_version.restype = ctypes.c_char_p
         _LIB = lib

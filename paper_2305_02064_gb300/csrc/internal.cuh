@@ -92,6 +92,9 @@ cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s);
 cudaError_t launch_peak(const void *vol, int64_t n, void *scratch, void *result, cudaStream_t s);
 size_t peak_scratch_bytes(int64_t n);
 
+// Record a formatted message for mmsar_last_error() and return `st`.
+mmsar_status report_error(mmsar_status st, const char *fmt, ...);
+
 // Raise a kernel's dynamic shared-memory limit once per device (the
 // attribute is per device; the first launch on each device sets it).
 cudaError_t ensure_smem_attr(const void *func, size_t bytes);

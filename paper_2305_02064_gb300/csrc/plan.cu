@@ -24,6 +24,16 @@ static mmsar_status fail(mmsar_status st, const char *fmt, ...) {
     return st;
 }
 
+mmsar_status report_error(mmsar_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
 static mmsar_status cuda_fail(cudaError_t e, const char *where) {
     return fail(MMSAR_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
