@@ -19,6 +19,7 @@ constexpr int kMaxNz = 256;
 // Error bits of the device error word (one per mmsar_status code).
 constexpr int kErrNonfinite = 1 << MMSAR_ERR_NONFINITE;
 constexpr int kErrGeometry = 1 << MMSAR_ERR_INVALID_ARG;
+constexpr int kErrTimeout = 1 << MMSAR_ERR_DEVICE_TIMEOUT;
 
 // Device-visible header at offset 0 of the workspace.
 struct WsHeader {
@@ -55,6 +56,7 @@ struct Plan {
     double tau_x, tau_y, tau_z;
     // workspace layout (byte offsets)
     size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm, off_srec;
+    size_t off_dd, off_wq;   // per sorted sample: in-bin cell offsets; Gaussian weight quads
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
     // optional per-stage timing events (caller-owned)
@@ -63,7 +65,7 @@ struct Plan {
 };
 
 constexpr int kStages = 8;
-constexpr int kKernelsPerImage = 12;
+constexpr int kKernelsPerImage = 13;
 
 }  // namespace mmsar
 
@@ -83,6 +85,7 @@ cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
+cudaError_t launch_spread_weights(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);

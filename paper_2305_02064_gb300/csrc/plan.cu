@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -61,23 +62,26 @@ static int width_for_tol(double tol) {
 
 cudaError_t ensure_smem_attr(const void *func, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    // the attribute is per device; a small per-kernel table of done devices
-    struct Entry { const void *f; unsigned long long devmask; };
-    static Entry table[64];
+    // The attribute is per device and per kernel; remember the largest value
+    // set for each (kernel, device) and raise it when a launch needs more.
+    struct Entry { const void *f; int dev; size_t bytes; };
+    static Entry table[256];
     static int used = 0;
+    static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    Entry *hit = nullptr;
     for (int i = 0; i < used; ++i)
-        if (table[i].f == func && (table[i].devmask >> (dev & 63) & 1ull)) return cudaSuccess;
+        if (table[i].f == func && table[i].dev == dev) hit = &table[i];
+    if (hit && hit->bytes >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < used; ++i)
-        if (table[i].f == func) {
-            table[i].devmask |= 1ull << (dev & 63);
-            return cudaSuccess;
-        }
-    if (used < 64) table[used++] = Entry{func, 1ull << (dev & 63)};
+    if (hit)
+        hit->bytes = bytes;
+    else if (used < 256)
+        table[used++] = Entry{func, dev, bytes};
     return cudaSuccess;
 }
 
@@ -149,6 +153,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_phase = take(sizeof(uint2) * L);
     p.off_perm = take(sizeof(int) * L);
     p.off_srec = take(sizeof(SampleRec) * L);
+    p.off_dd = take(sizeof(int) * L);
+    p.off_wq = take(sizeof(float4) * (size_t)(2 * p.w + 7) * L);
     p.off_shat = take(sizeof(float2) * (size_t)p.n_kc * L * kKC);
     const size_t G = sizeof(float2) * (size_t)p.n_kc * p.mry * p.mrx * kKC;
     const size_t S = sizeof(float2) * (size_t)p.mx * p.my * p.nkp;
@@ -273,6 +279,7 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_STEP(launch_bin_scan(p, workspace, s), "bin scan");
     MMSAR_STEP(launch_bin_scatter(p, workspace, s), "bin scatter");
     MMSAR_STEP(launch_bin_sort(p, workspace, s), "bin sort");
+    MMSAR_STEP(launch_spread_weights(p, workspace, s), "gridding weights");
     MMSAR_MARK(1);
     MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation");
     MMSAR_MARK(2);
@@ -306,6 +313,8 @@ mmsar_status mmsar_poll_error(const void *workspace, void *stream) {
         if (e != cudaSuccess) return cuda_fail(e, "clearing the error word");
     }
     if (word & kErrNonfinite) return fail(MMSAR_ERR_NONFINITE, "non-finite value in the echo or the geometry");
+    if (word & kErrTimeout)
+        return fail(MMSAR_ERR_DEVICE_TIMEOUT, "a bounded device-side wait for an asynchronous copy gave up");
     if (word & kErrGeometry)
         return fail(MMSAR_ERR_INVALID_ARG, "z_scene does not lie beyond the reference plane z_ref (Z_c <= 0)");
     if (word) return fail(MMSAR_ERR_CUDA, "device error word 0x%x", word);

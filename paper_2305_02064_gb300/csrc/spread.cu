@@ -2,41 +2,104 @@
 // that Sec. III uses for FT_2D of Eq. 16) of the compensated virtual-array
 // samples onto the 2Mx x 2My periodic aperture grid, in gather form.
 //
-// Work decomposition: a CTA owns a 16x16 tile of grid cells and one chunk of
-// 32 frequencies; each of its 16 warps owns a 4x4 block of cells and keeps the
-// 16 complex accumulators of its lane's frequency in registers.  A warp visits
-// only the bins (4x4 cells each, samples sorted by bin) whose samples can
-// reach its block, so no two warps ever write the same cell and no atomics
-// are used.  The Gaussian weights depend on the sample only, so each lane
-// applies the same 8 weights (4 per axis) to its own frequency.
-//
 // Weight of a sample at grid position g for cell j: exp(-kappa (g - j)^2)
 // with kappa = h^2 / (4 tau) = 1.5 pi / w for the Greengard-Lee tau and a
 // cell size h = 2 pi / (2M); the sample reaches the w cells
-// ceil(g - w/2) .. ceil(g - w/2) + w - 1 (indices modulo the grid size).
+// u0 .. u0 + w - 1, u0 = ceil(g - w/2) (indices modulo the grid size).
+//
+// spread_weights_kernel (once per sample, bin order): the sample's offset
+// inside its 4x4-cell bin and, per axis, w + 3 "quads" -- quad q holds the
+// weights of taps q-3 .. q (zero outside 0..w-1), i.e. exactly the four
+// weights a 4-cell block needs when it starts q - 3 cells after u0.
+//
+// spread_kernel: a CTA owns a 16x16 tile of grid cells and one chunk of 32
+// frequencies; each of its 16 warps owns a 4x4 block of cells and keeps the
+// 16 complex accumulators of its lane's frequency in registers.  Warps work
+// independently (no block barrier): a warp walks the bins whose samples can
+// reach its block, tests 32 samples at a time (one lane each) for overlap with
+// the block and keeps the overlapping ones in a ballot mask, then applies them
+// one by one with the loads of the next one already in flight.  For a bin d
+// bins before the block, the block starts 4 d - (in-bin offset) cells after
+// the sample's first tap, which selects one weight quad per axis (two 16-byte
+// broadcast loads).  No two warps write the same cell: no atomics, a fixed
+// summation order.
 #include "fft.cuh"
 #include "internal.cuh"
 
 namespace mmsar {
 
+__global__ void __launch_bounds__(256) spread_weights_kernel(const SampleRec *__restrict__ srec,
+                                                             const WsHeader *__restrict__ hdr, int w, float kappa,
+                                                             int *__restrict__ dd, float4 *__restrict__ wrec) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= hdr->n_valid) return;
+    const SampleRec r = srec[s];
+    const int nq = w + 3;
+    float4 *out = wrec + (long long)s * (2 * nq + 1);
+    const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
+    dd[s] = d;
+    out[0] = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
+    float wx[18], wy[18];   // taps -3 .. 14 (w <= 12)
+#pragma unroll
+    for (int a = 0; a < 18; ++a) {
+        const int tap = a - 3;
+        const float dxa = r.fx - (float)tap, dyb = r.fy - (float)tap;
+        const bool in = tap >= 0 && tap < w;
+        wx[a] = in ? expf(-kappa * dxa * dxa) : 0.f;
+        wy[a] = in ? expf(-kappa * dyb * dyb) : 0.f;
+    }
+    for (int q = 0; q < nq; ++q) {
+        // quad q = taps q-3 .. q = entries q .. q+3 of the padded arrays
+        float4 x, y;
+        switch (q) {   // keep the register arrays statically indexed
+#define MMSAR_Q(Q)                                                              \
+    case Q:                                                                      \
+        x = make_float4(wx[Q], wx[(Q) + 1], wx[(Q) + 2], wx[(Q) + 3]);           \
+        y = make_float4(wy[Q], wy[(Q) + 1], wy[(Q) + 2], wy[(Q) + 3]);           \
+        break;
+            MMSAR_Q(0) MMSAR_Q(1) MMSAR_Q(2) MMSAR_Q(3) MMSAR_Q(4) MMSAR_Q(5) MMSAR_Q(6) MMSAR_Q(7)
+            MMSAR_Q(8) MMSAR_Q(9) MMSAR_Q(10) MMSAR_Q(11) MMSAR_Q(12) MMSAR_Q(13) MMSAR_Q(14)
+#undef MMSAR_Q
+            default: x = y = make_float4(0.f, 0.f, 0.f, 0.f); break;
+        }
+        out[1 + q] = x;
+        out[1 + nq + q] = y;
+    }
+}
+
+cudaError_t launch_spread_weights(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    const unsigned blocks = (unsigned)((p.L + 255) / 256);
+    spread_weights_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const SampleRec *>(w + p.off_srec),
+                                                 reinterpret_cast<const WsHeader *>(w), p.w,
+                                                 (float)(1.5 * kPi / p.w), reinterpret_cast<int *>(w + p.off_dd),
+                                                 reinterpret_cast<float4 *>(w + p.off_wq));
+    return cudaGetLastError();
+}
+
 struct SpreadArgs {
     const float2 *shat;       // [n_kc][Lmax][32], bin order
-    const SampleRec *srec;    // [Lmax], bin order
+    const int *dd;            // [Lmax] in-bin offsets du | dv << 2, bin order
+    const float4 *wrec;       // [Lmax][2 (w + 3) + 1]: header + x quads + y quads
     const int *offsets;       // [n_bins + 1]
     float2 *G;                // [n_kc][mry][mrx][32]
     long long Lmax;
     int mrx, mry, nbx, nby;
-    int w, nb;                // taps per axis; bins visited per axis
-    float kappa;
+    int w, nb, n_kc;          // taps per axis; bins visited per axis; frequency chunks
 };
 
-__global__ void __launch_bounds__(512, 2) spread_kernel(SpreadArgs a) {
+constexpr int kSpreadThreads = 512;
+
+__global__ void __launch_bounds__(kSpreadThreads, 2) spread_kernel(SpreadArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx >> 4;
-    const int kc = blockIdx.y;
-    const int U = (blockIdx.x % tiles_x) * 16 + (warp & 3) * 4;
-    const int V = (blockIdx.x / tiles_x) * 16 + (warp >> 2) * 4;
-    const int half_x = a.mrx >> 1, half_y = a.mry >> 1;
+    // the frequency chunk varies fastest, so the chunks of one tile run
+    // together and share the tile's weight records in L2
+    const int kc = blockIdx.x % a.n_kc;
+    const int tile = blockIdx.x / a.n_kc;
+    const int U = (tile % tiles_x) * 16 + (warp & 3) * 4;
+    const int V = (tile / tiles_x) * 16 + (warp >> 2) * 4;
+    const int rq = 2 * (a.w + 3) + 1;
     float2 acc[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -52,30 +115,56 @@ __global__ void __launch_bounds__(512, 2) spread_kernel(SpreadArgs a) {
             if (bu < 0) bu += a.nbx;
             const int bin = bv * a.nbx + bu;
             const int beg = __ldg(a.offsets + bin), end = __ldg(a.offsets + bin + 1);
-            for (int s = beg; s < end; ++s) {
-                const SampleRec r = a.srec[s];
-                int ru = U - r.u0;
-                if (ru > half_x) ru -= a.mrx; else if (ru <= -half_x) ru += a.mrx;
-                int rv = V - r.v0;
-                if (rv > half_y) rv -= a.mry; else if (rv <= -half_y) rv += a.mry;
-                if (ru < -3 || ru >= a.w || rv < -3 || rv >= a.w) continue;
-                float wx[4], wy[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int ta = ru + i, tb = rv + i;
-                    const float dxa = r.fx - (float)ta, dyb = r.fy - (float)tb;
-                    wx[i] = (ta >= 0 && ta < a.w) ? __expf(-a.kappa * dxa * dxa) : 0.f;
-                    wy[i] = (tb >= 0 && tb < a.w) ? __expf(-a.kappa * dyb * dyb) : 0.f;
+            for (int s0 = beg; s0 < end; s0 += 32) {
+                // which of the next 32 samples reach this block, in one step
+                const int my = s0 + lane;
+                int ru = 0, rv = 0;
+                bool rel = false;
+                if (my < end) {
+                    const int d = __ldg(a.dd + my);
+                    ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
+                    rv = 4 * dbv - (d >> 2);
+                    rel = ru < a.w && rv < a.w;
                 }
-                const float2 v = __ldg(sh + (long long)s * kKC);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 t = make_float2(wy[j] * v.x, wy[j] * v.y);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        acc[j][i].x = fmaf(wx[i], t.x, acc[j][i].x);
-                        acc[j][i].y = fmaf(wx[i], t.y, acc[j][i].y);
+                const int packed = (ru + 3) | ((rv + 3) << 8);
+                unsigned mask = __ballot_sync(0xffffffffu, rel);
+                if (!mask) continue;
+                // software pipeline: the loads of the next relevant sample are
+                // in flight while the current one is accumulated
+                int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                int pk = __shfl_sync(0xffffffffu, packed, src);
+                long long sidx = s0 + src;
+                const float4 *rp = a.wrec + sidx * rq + 1;
+                float4 qx = __ldg(rp + (pk & 0xff));
+                float4 qy = __ldg(rp + (a.w + 3) + (pk >> 8));
+                float2 v = __ldg(sh + sidx * kKC);
+                while (true) {
+                    const float4 cx = qx, cy = qy;
+                    const float2 cv = v;
+                    const bool more = mask != 0;
+                    if (more) {
+                        src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        pk = __shfl_sync(0xffffffffu, packed, src);
+                        sidx = s0 + src;
+                        rp = a.wrec + sidx * rq + 1;
+                        qx = __ldg(rp + (pk & 0xff));
+                        qy = __ldg(rp + (a.w + 3) + (pk >> 8));
+                        v = __ldg(sh + sidx * kKC);
                     }
+                    const float wx[4] = {cx.x, cx.y, cx.z, cx.w};
+                    const float wy[4] = {cy.x, cy.y, cy.z, cy.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 t = make_float2(wy[j] * cv.x, wy[j] * cv.y);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            acc[j][i].x = fmaf(wx[i], t.x, acc[j][i].x);
+                            acc[j][i].y = fmaf(wx[i], t.y, acc[j][i].y);
+                        }
+                    }
+                    if (!more) break;
                 }
             }
         }
@@ -91,7 +180,8 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
     SpreadArgs a;
     a.shat = reinterpret_cast<const float2 *>(w + p.off_shat);
-    a.srec = reinterpret_cast<const SampleRec *>(w + p.off_srec);
+    a.dd = reinterpret_cast<const int *>(w + p.off_dd);
+    a.wrec = reinterpret_cast<const float4 *>(w + p.off_wq);
     a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
     a.G = reinterpret_cast<float2 *>(w + p.off_G);
     a.Lmax = p.L;
@@ -101,9 +191,9 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.nby = p.nby;
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
-    a.kappa = (float)(1.5 * kPi / p.w);
-    dim3 grid((unsigned)((p.mrx / 16) * (p.mry / 16)), p.n_kc);
-    spread_kernel<<<grid, 512, 0, s>>>(a);
+    a.n_kc = p.n_kc;
+    const unsigned blocks = (unsigned)((p.mrx / 16) * (p.mry / 16) * p.n_kc);
+    spread_kernel<<<blocks, kSpreadThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

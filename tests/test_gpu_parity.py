@@ -199,3 +199,16 @@ def test_stage_events_time_every_stage(dev, tiny_scan):
     plan.set_stage_events(None)
     plan.image(ws, *args, vol)
     plan.poll_error(ws)
+
+
+@pytest.mark.parametrize("tol,w,bound", [(2e-3, 5, 6e-5), (2e-4, 7, 7e-7), (1e-5, 10, 1e-8), (1e-6, 12, 1e-8)])
+def test_kernel_widths(dev, tiny_scan, tol, w, bound):
+    """Every Gaussian width the plan can pick: the NMSE follows the predicted
+    gridding error (~3 transforms x err(w)^2, x10 margin), down to the FP32
+    floor."""
+    got, plan = run_gpu(tiny_scan, dev, nufft_tol=tol)
+    assert plan.kernel_width == w
+    ref = oracle_of(tiny_scan)
+    e = rma.nmse(got, ref)
+    assert e <= bound, e
+    assert rma.peak_index(got) == rma.peak_index(ref)
