@@ -1,4 +1,5 @@
-// Shared-memory Stockham FFT along the row axis of a [L][C] tile.
+// Shared-memory Stockham FFT along the row axis of a [L][P] tile (C columns,
+// row pitch P).
 //
 // The tile holds C independent columns (contiguous in shared memory, so a
 // warp's lanes touch consecutive 8-byte words and the accesses are
@@ -83,7 +84,7 @@ __device__ __forceinline__ void fill_twiddles(float2 *tw, int tid, int nt) {
     }
 }
 
-template <int L, int R, int NS, int C, int NT, int SIGN>
+template <int L, int R, int NS, int C, int P, int NT, int SIGN>
 __device__ __forceinline__ void fft_pass(float2 *buf, const float2 *tw) {
     constexpr int NJ = L / R;
     constexpr int TOTAL = NJ * C;
@@ -96,7 +97,7 @@ __device__ __forceinline__ void fft_pass(float2 *buf, const float2 *tw) {
         if (TOTAL % NT == 0 || item < TOTAL) {
             const int j = item / C, c = item - (item / C) * C;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * NJ) * C + c];
+            for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * NJ) * P + c];
             if constexpr (NS > 1) {
                 const int k = j % NS;
 #pragma unroll
@@ -114,28 +115,34 @@ __device__ __forceinline__ void fft_pass(float2 *buf, const float2 *tw) {
             const int k = j % NS;
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[(base + r * NS) * C + c] = v[it][r];
+            for (int r = 0; r < R; ++r) buf[(base + r * NS) * P + c] = v[it][r];
         }
     }
     __syncthreads();
 }
 
-template <int L, int NS, int C, int NT, int SIGN>
+template <int L, int NS, int C, int P, int NT, int SIGN>
 struct FftRun {
     static __device__ __forceinline__ void run(float2 *buf, const float2 *tw) {
         if constexpr (NS < L) {
             constexpr int R = pick_radix(L / NS);
-            fft_pass<L, R, NS, C, NT, SIGN>(buf, tw);
-            FftRun<L, NS * R, C, NT, SIGN>::run(buf, tw);
+            fft_pass<L, R, NS, C, P, NT, SIGN>(buf, tw);
+            FftRun<L, NS * R, C, P, NT, SIGN>::run(buf, tw);
         }
     }
 };
 
-// Transform all C columns of buf[L][C] in place.  Every thread of the block
-// (NT of them) must call it; the caller synchronises before the first call.
-template <int L, int C, int NT, int SIGN>
+// Row pitch (in complex elements) of a tile with C columns: one extra element
+// when a warp spans several rows, so that the rows a warp touches in one
+// access fall on different shared-memory banks.
+__host__ __device__ constexpr int fft_pitch(int C) { return C >= 32 ? C : C + 1; }
+
+// Transform all C columns of buf[L][P] (row pitch P >= C) in place.  Every
+// thread of the block (NT of them) must call it; the caller synchronises
+// before the first call.
+template <int L, int C, int NT, int SIGN, int P = fft_pitch(C)>
 __device__ __forceinline__ void smem_fft(float2 *buf, const float2 *tw) {
-    FftRun<L, 1, C, NT, SIGN>::run(buf, tw);
+    FftRun<L, 1, C, P, NT, SIGN>::run(buf, tw);
 }
 
 }  // namespace mmsar

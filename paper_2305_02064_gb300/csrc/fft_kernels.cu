@@ -22,14 +22,28 @@ __host__ __device__ constexpr int fft_cols(int L) { return L >= 256 ? 8192 / L :
 template <int L, int SIGN>
 __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     constexpr int C = fft_cols(L);
+    constexpr int P = fft_pitch(C);
     extern __shared__ float2 smem[];
     float2 *tile = smem;
-    float2 *tw = smem + L * C;
+    float2 *tw = smem + L * P;
     const int tid = threadIdx.x;
     const int nchunks = (a.ncols + C - 1) / C;
     const int chunk = blockIdx.x % nchunks;
     const int t2 = blockIdx.x / nchunks;
     const int t1 = blockIdx.y;
+    if (a.tile_win) {
+        const int len = a.tile_win[1];
+        if (len < a.nt2) {
+            int d = (t2 - a.tile_win[0]) % a.nt2;
+            if (d < 0) d += a.nt2;
+            if (d >= len) return;   // a row that is known to be zero: nothing to do
+        }
+    }
+    int wlo = 0, wlen = a.n_in;
+    if (a.in_win) {
+        wlo = a.in_win[0];
+        wlen = a.in_win[1];
+    }
     const int c0 = chunk * C;
     const int cw = min(C, a.ncols - c0);
     const float2 *in = a.in + t1 * a.in_t1 + t2 * a.in_t2 + c0;
@@ -38,7 +52,10 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     for (int e = tid; e < L * C; e += kFftThreads) {
         const int f = e / C, c = e - (e / C) * C;
         const int r = (f - a.in_shift) & (L - 1);
-        tile[e] = (r < a.n_in && c < cw) ? __ldg(in + (long long)r * a.in_row + c) : make_float2(0.f, 0.f);
+        int d = r - wlo;
+        if (d < 0) d += a.n_in;
+        const bool live = r < a.n_in && c < cw && d < wlen;
+        tile[f * P + c] = live ? __ldg(in + (long long)r * a.in_row + c) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     smem_fft<L, C, kFftThreads, SIGN>(tile, tw);
@@ -49,7 +66,7 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
             const int f = o - half;
             float sc = a.scale;
             if (a.gauss_tau > 0.f) sc *= __expf((float)(f * f) * a.gauss_tau);
-            const float2 v = tile[(f & (L - 1)) * C + c];
+            const float2 v = tile[(f & (L - 1)) * P + c];
             out[(long long)o * a.out_row + c] = make_float2(v.x * sc, v.y * sc);
         }
     }
@@ -58,7 +75,7 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
 template <int L, int SIGN>
 static cudaError_t launch_L(const ColumnFFT &a, cudaStream_t s) {
     constexpr int C = fft_cols(L);
-    const size_t smem = (size_t)(L * C + L) * sizeof(float2);
+    const size_t smem = (size_t)(L * fft_pitch(C) + L) * sizeof(float2);
     cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN>, smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (a.ncols + C - 1) / C;
@@ -112,6 +129,9 @@ cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s) {
     u.nt2 = p.mry;
     u.scale = (float)(std::sqrt(kPi / p.tau_x) / p.mrx);
     u.gauss_tau = (float)p.tau_x;
+    const WsHeader *hdr = reinterpret_cast<const WsHeader *>(w);
+    u.in_win = &hdr->u_lo;     // cells of a row outside the occupied window are zero
+    u.tile_win = &hdr->v_lo;   // rows outside it are zero: skipped, A left unwritten
     return launch_column_fft(u, s);
 }
 
@@ -139,6 +159,8 @@ cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s) {
     v.nt2 = p.mx;
     v.scale = (float)(std::sqrt(kPi / p.tau_y) / p.mry);
     v.gauss_tau = (float)p.tau_y;
+    v.in_win = &reinterpret_cast<const WsHeader *>(w)->v_lo;   // only the occupied rows of A
+    v.tile_win = nullptr;
     return launch_column_fft(v, s);
 }
 
@@ -168,6 +190,8 @@ cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s) {
     a.nt2 = p.mx;
     a.scale = 1.0f;
     a.gauss_tau = 0.f;
+    a.in_win = nullptr;
+    a.tile_win = nullptr;
     return launch_column_fft(a, s);
 }
 
@@ -195,6 +219,8 @@ cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s) {
     b.nt2 = ny;
     b.scale = (float)(1.0 / ((double)p.L * p.shape.n_k));
     b.gauss_tau = 0.f;
+    b.in_win = nullptr;
+    b.tile_win = nullptr;
     return launch_column_fft(b, s);
 }
 

@@ -26,7 +26,12 @@ struct WsHeader {
     int error;          // OR of kErr* bits
     int n_valid;        // samples that were binned
     double z_ref;       // resolved reference plane
-    double pad[14];
+    // first gridding cell of any sample, unwrapped (min / max over samples)
+    int u_min, u_max, v_min, v_max;
+    // occupied window of the periodic gridding grid: cells lo .. lo + len - 1
+    // (mod the grid size) can be nonzero; everything else is known zero
+    int u_lo, u_len, v_lo, v_len;
+    double pad[10];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 
@@ -118,6 +123,11 @@ struct ColumnFFT {
     long long out_row, out_t1, out_t2;
     int ncols;          // contiguous columns per tile
     int nt1, nt2;       // tile counts
+    // optional device windows (lo, len), periodic: input rows outside
+    // in_win (period n_in) are taken as zero without being read; tiles t2
+    // outside tile_win (period nt2) are skipped entirely (nothing written)
+    const int *in_win;
+    const int *tile_win;
     float scale;
     float gauss_tau;
 };

@@ -13,7 +13,8 @@
 // f0 beta / c, df beta / c reduced to [0, 1) turns and stored as uint32
 // fixed point).  Per (sample, k) the phase a + k b is formed exactly in
 // wrapping 32-bit integer arithmetic, so its error is at most (1 + k) 2^-33
-// turns, and only the final sincospi runs in FP32.
+// turns; the final sine/cosine of the reduced angle (in [-pi, pi)) runs in
+// FP32 on the special-function unit.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -29,6 +30,10 @@ __global__ void __launch_bounds__(1024) zref_kernel(const double *__restrict__ p
                                                     double z_given, WsHeader *hdr) {
     __shared__ double red[1024];
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        hdr->u_min = hdr->v_min = 0x7fffffff;
+        hdr->u_max = hdr->v_max = -0x7fffffff - 1;
+    }
     if (given) {
         if (tid == 0) hdr->z_ref = z_given;
         return;
@@ -80,9 +85,22 @@ __device__ __forceinline__ uint32_t frac_to_fixed(double turns) {
     return (uint32_t)(unsigned long long)llrint(f * 4294967296.0);  // 2^32 wraps to 0
 }
 
-__global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= a.L) return;
+__device__ __forceinline__ void box_reduce(int umin, int umax, int vmin, int vmax, WsHeader *hdr) {
+    for (int o = 16; o > 0; o >>= 1) {
+        umin = min(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+        umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if ((threadIdx.x & 31) == 0 && umin <= umax) {
+        atomicMin(&hdr->u_min, umin);
+        atomicMax(&hdr->u_max, umax);
+        atomicMin(&hdr->v_min, vmin);
+        atomicMax(&hdr->v_max, vmax);
+    }
+}
+
+__device__ void geometry_one(const GeomArgs &a, long long l, int &umin, int &umax, int &vmin, int &vmax) {
     const int p = (int)(l % a.P);
     const int r = (int)((l / a.P) % a.R);
     const int t = (int)(l / ((long long)a.P * a.R));
@@ -114,6 +132,13 @@ __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
     const double gy = (yv - a.y_c) * a.inv_dy2;
     const double u0d = ceil(gx - a.half_w), v0d = ceil(gy - a.half_w);
     const double fx = gx - u0d, fy = gy - v0d;
+    // occupied window; a sample absurdly far away (beyond 1e9 cells) makes the
+    // window the whole grid
+    const bool ufar = fabs(u0d) > 1.0e9, vfar = fabs(v0d) > 1.0e9;
+    umin = ufar ? -1073741824 : (int)u0d;
+    umax = ufar ? 1073741823 : (int)u0d;
+    vmin = vfar ? -1073741824 : (int)v0d;
+    vmax = vfar ? 1073741823 : (int)v0d;
     long long u0 = (long long)u0d % a.mrx, v0 = (long long)v0d % a.mry;
     if (u0 < 0) u0 += a.mrx;
     if (v0 < 0) v0 += a.mry;
@@ -128,6 +153,15 @@ __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
     const int bin = (rc.v0 / kBin) * a.nbx + rc.u0 / kBin;
     a.binid[l] = bin;
     atomicAdd(&a.counts[bin], 1);
+}
+
+__global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int bumin = 0x7fffffff, bumax = -0x7fffffff - 1, bvmin = 0x7fffffff, bvmax = -0x7fffffff - 1;
+    if (l < a.L) {
+        geometry_one(a, l, bumin, bumax, bvmin, bvmax);
+    }
+    box_reduce(bumin, bumax, bvmin, bvmax, a.hdr);
 }
 
 cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
@@ -166,10 +200,35 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
 // ------------------------------------------------------------------ bin scan
 // Exclusive prefix sum of the bin counts (one block); also seeds the scatter
 // cursors and records the number of binned samples.
+// Occupied window of one axis from the min / max first cell: cells
+// lo .. lo + len - 1 (mod m) can receive a tap.
+__device__ __forceinline__ void finish_window(int vmin, int vmax, int w, int m, int *lo, int *len) {
+    if (vmin > vmax) {          // no sample
+        *lo = 0;
+        *len = 0;
+        return;
+    }
+    const long long span = (long long)vmax - vmin + w;
+    if (span >= m) {
+        *lo = 0;
+        *len = m;
+        return;
+    }
+    int l0 = vmin % m;
+    if (l0 < 0) l0 += m;
+    *lo = l0;
+    *len = (int)span;
+}
+
 __global__ void __launch_bounds__(1024) bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets,
-                                                        int *__restrict__ cursor, long long n, WsHeader *hdr) {
+                                                        int *__restrict__ cursor, long long n, WsHeader *hdr, int w,
+                                                        int mrx, int mry) {
     __shared__ int part[1024];
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        finish_window(hdr->u_min, hdr->u_max, w, mrx, &hdr->u_lo, &hdr->u_len);
+        finish_window(hdr->v_min, hdr->v_max, w, mry, &hdr->v_lo, &hdr->v_len);
+    }
     const long long per = (n + 1023) / 1024;
     const long long b0 = tid * per, b1 = min(n, b0 + per);
     int s = 0;
@@ -200,7 +259,7 @@ cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s) {
     bin_scan_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts),
                                        reinterpret_cast<int *>(w + p.off_offsets),
                                        reinterpret_cast<int *>(w + p.off_cursor), p.n_bins,
-                                       reinterpret_cast<WsHeader *>(w));
+                                       reinterpret_cast<WsHeader *>(w), p.w, p.mrx, p.mry);
     return cudaGetLastError();
 }
 
@@ -281,9 +340,27 @@ cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ compensate
-// One warp per (sorted slot, k-chunk): lane k reads s[l][k] (256 coalesced
-// bytes per warp), rotates it by exp(+j 2 pi (a + k b)) and writes
-// s_hat[kc][slot][lane].
+// One warp per group of kCompUnroll sorted slots and one k-chunk: lane k
+// reads s[l][k] for each slot of the group (the loads of the group are
+// issued together, 256 coalesced bytes each), rotates it by
+// exp(+j 2 pi (a + k b)) and writes s_hat[kc][slot][lane].
+constexpr int kCompUnroll = 4;
+
+template <int DT>
+__device__ __forceinline__ float2 load_echo(const void *__restrict__ echo_v, long long e, float scale) {
+    if (DT == MMSAR_ECHO_C64) {
+        return __ldg(reinterpret_cast<const float2 *>(echo_v) + e);
+    } else if (DT == MMSAR_ECHO_F16X2_SCALED) {
+        const __half2 h = reinterpret_cast<const __half2 *>(echo_v)[e];
+        float2 v = __half22float2(h);
+        return make_float2(v.x * scale, v.y * scale);
+    } else {
+        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162 *>(echo_v)[e];
+        float2 v = __bfloat1622float2(h);
+        return make_float2(v.x * scale, v.y * scale);
+    }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(256) compensate_kernel(const void *__restrict__ echo_v,
                                                          const float *__restrict__ scale_p,
@@ -298,43 +375,50 @@ __global__ void __launch_bounds__(256) compensate_kernel(const void *__restrict_
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *scale_p;
     bool bad = false;
-    for (long long slot = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; slot < n_valid;
-         slot += warps) {
-        const int l = perm[slot];
-        float2 v = make_float2(0.f, 0.f);
-        if (k < Nk) {
-            const long long e = (long long)l * Nk + k;
-            if (DT == MMSAR_ECHO_C64) {
-                v = __ldg(reinterpret_cast<const float2 *>(echo_v) + e);
-            } else if (DT == MMSAR_ECHO_F16X2_SCALED) {
-                const __half2 h = reinterpret_cast<const __half2 *>(echo_v)[e];
-                v = __half22float2(h);
-                v.x *= scale;
-                v.y *= scale;
-            } else {
-                const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162 *>(echo_v)[e];
-                v = __bfloat1622float2(h);
-                v.x *= scale;
-                v.y *= scale;
-            }
-            bad |= !(isfinite(v.x) && isfinite(v.y));
-            const uint2 ph = phase[l];
-            const uint32_t turns = ph.x + (uint32_t)k * ph.y;      // exact mod 2^32
-            const float tf = (float)(int32_t)turns * 4.6566128730773926e-10f;  // [-1, 1): 2 * turns / 2^32
-            float sn, cs;
-            sincospif(tf, &sn, &cs);
-            v = cmul(v, make_float2(cs, sn));
+    for (long long g0 = ((long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * kCompUnroll; g0 < n_valid;
+         g0 += warps * kCompUnroll) {
+        int l[kCompUnroll];
+        uint2 ph[kCompUnroll];
+        float2 v[kCompUnroll];
+#pragma unroll
+        for (int u = 0; u < kCompUnroll; ++u) {
+            const long long slot = g0 + u;
+            l[u] = slot < n_valid ? __ldg(perm + slot) : -1;
         }
-        shat[((long long)kc * Lmax + slot) * kKC + lane] = v;
+#pragma unroll
+        for (int u = 0; u < kCompUnroll; ++u) {
+            v[u] = make_float2(0.f, 0.f);
+            ph[u] = make_uint2(0u, 0u);
+            if (l[u] >= 0) {
+                ph[u] = __ldg(phase + l[u]);
+                if (k < Nk) v[u] = load_echo<DT>(echo_v, (long long)l[u] * Nk + k, scale);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kCompUnroll; ++u) {
+            if (l[u] < 0) continue;
+            float2 out = make_float2(0.f, 0.f);
+            if (k < Nk) {
+                bad |= !(isfinite(v[u].x) && isfinite(v[u].y));
+                const uint32_t turns = ph[u].x + (uint32_t)k * ph[u].y;            // exact mod 2^32
+                // the angle is already reduced to [-pi, pi): the hardware sine and
+                // cosine (absolute error ~4e-7 there) are accurate enough
+                const float ang = (float)(int32_t)turns * 1.4629180792671596e-09f;  // 2 pi turns / 2^32
+                float sn, cs;
+                __sincosf(ang, &sn, &cs);
+                out = cmul(v[u], make_float2(cs, sn));
+            }
+            __stcs(shat + ((long long)kc * Lmax + g0 + u) * kKC + lane, out);
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, kErrNonfinite);
 }
 
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const long long warps_needed = p.L;
+    const long long warps_needed = (p.L + kCompUnroll - 1) / kCompUnroll;
     long long blocks = (warps_needed + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > 152 * 32) blocks = 152 * 32;
     dim3 grid((unsigned)blocks, p.n_kc);
     const int *perm = reinterpret_cast<int *>(w + p.off_perm);
     const uint2 *ph = reinterpret_cast<uint2 *>(w + p.off_phase);

@@ -12,13 +12,13 @@
 // weights of taps q-3 .. q (zero outside 0..w-1), i.e. exactly the four
 // weights a 4-cell block needs when it starts q - 3 cells after u0.
 //
-// spread_kernel: a CTA owns a 16x16 tile of grid cells and one chunk of 32
-// frequencies; each of its 16 warps owns a 4x4 block of cells and keeps the
+// spread_kernel: a CTA owns a 16x8 tile of grid cells and one chunk of 32
+// frequencies; each of its 8 warps owns a 4x4 block of cells and keeps the
 // 16 complex accumulators of its lane's frequency in registers.  Warps work
 // independently (no block barrier): a warp walks the bins whose samples can
 // reach its block, tests 32 samples at a time (one lane each) for overlap with
-// the block and keeps the overlapping ones in a ballot mask, then applies them
-// one by one with the loads of the next one already in flight.  For a bin d
+// the block and appends the overlapping ones to a list in shared memory, then
+// applies the list with the loads of the entry two ahead already in flight.  For a bin d
 // bins before the block, the block starts 4 d - (in-bin offset) cells after
 // the sample's first tap, which selects one weight quad per axis (two 16-byte
 // broadcast loads).  No two warps write the same cell: no atomics, a fixed
@@ -83,30 +83,95 @@ struct SpreadArgs {
     const float4 *wrec;       // [Lmax][2 (w + 3) + 1]: header + x quads + y quads
     const int *offsets;       // [n_bins + 1]
     float2 *G;                // [n_kc][mry][mrx][32]
+    const WsHeader *hdr;      // occupied window of the grid
     long long Lmax;
     int mrx, mry, nbx, nby;
     int w, nb, n_kc;          // taps per axis; bins visited per axis; frequency chunks
 };
 
-constexpr int kSpreadThreads = 512;
+// Does [t0, t0 + span) meet the periodic window lo .. lo + len - 1 (mod m)?
+__device__ __forceinline__ bool tile_meets(int t0, int span, int lo, int len, int m) {
+    if (len >= m) return true;
+    if (len <= 0) return false;
+    int d = (t0 - lo) % m;
+    if (d < 0) d += m;
+    int e = (lo - t0) % m;
+    if (e < 0) e += m;
+    return d < len || e < span;
+}
 
-__global__ void __launch_bounds__(kSpreadThreads, 2) spread_kernel(SpreadArgs a) {
+constexpr int kSpreadThreads = 256;   // 8 warps: a 16 x 8-cell tile
+
+constexpr int kListCap = 256;   // relevant samples listed per warp before they are applied
+
+__global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a) {
+    __shared__ int2 lists[kSpreadThreads / 32][kListCap];   // (sample, quad offsets) per warp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx >> 4;
     // the frequency chunk varies fastest, so the chunks of one tile run
     // together and share the tile's weight records in L2
     const int kc = blockIdx.x % a.n_kc;
     const int tile = blockIdx.x / a.n_kc;
+    // tiles outside the occupied window stay unwritten: the FFT along x'
+    // reads only the window and takes the rest as zero
+    if (!tile_meets((tile % tiles_x) * 16, 16, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
+        !tile_meets((tile / tiles_x) * 8, 8, a.hdr->v_lo, a.hdr->v_len, a.mry))
+        return;
     const int U = (tile % tiles_x) * 16 + (warp & 3) * 4;
-    const int V = (tile / tiles_x) * 16 + (warp >> 2) * 4;
+    const int V = (tile / tiles_x) * 8 + (warp >> 2) * 4;
     const int rq = 2 * (a.w + 3) + 1;
+    const int nq = a.w + 3;
     float2 acc[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[j][i] = make_float2(0.f, 0.f);
     const float2 *sh = a.shat + (long long)kc * a.Lmax * kKC + lane;
+    int2 *list = lists[warp];
+
+    // apply the listed samples; the loads of entry i + 2 are issued while
+    // entry i is accumulated
+    auto apply = [&](int n) {
+        float4 xA, yA, xB, yB;
+        float2 vA, vB;
+        auto fetch = [&](int i, float4 &x, float4 &y, float2 &v) {
+            const int2 e = list[i];
+            const float4 *rp = a.wrec + (long long)e.x * rq + 1;
+            x = __ldg(rp + (e.y & 0xff));
+            y = __ldg(rp + nq + (e.y >> 8));
+            v = __ldg(sh + (long long)e.x * kKC);
+        };
+        auto consume = [&](const float4 &x, const float4 &y, const float2 &v) {
+            const float wx[4] = {x.x, x.y, x.z, x.w};
+            const float wy[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 t = make_float2(wy[j] * v.x, wy[j] * v.y);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[j][i].x = fmaf(wx[i], t.x, acc[j][i].x);
+                    acc[j][i].y = fmaf(wx[i], t.y, acc[j][i].y);
+                }
+            }
+        };
+        if (n > 0) fetch(0, xA, yA, vA);
+        if (n > 1) fetch(1, xB, yB, vB);
+        for (int i = 0; i < n; i += 2) {
+            const float4 cx = xA, cy = yA;
+            const float2 cv = vA;
+            if (i + 2 < n) fetch(i + 2, xA, yA, vA);
+            consume(cx, cy, cv);
+            if (i + 1 >= n) break;
+            const float4 dx = xB, dy = yB;
+            const float2 dv = vB;
+            if (i + 3 < n) fetch(i + 3, xB, yB, vB);
+            consume(dx, dy, dv);
+        }
+    };
+
     const int bu0 = U >> 2, bv0 = V >> 2;
+    const unsigned lt = (1u << lane) - 1u;
+    int n = 0;
     for (int dbv = a.nb - 1; dbv >= 0; --dbv) {
         int bv = bv0 - dbv;
         if (bv < 0) bv += a.nby;
@@ -118,57 +183,29 @@ __global__ void __launch_bounds__(kSpreadThreads, 2) spread_kernel(SpreadArgs a)
             for (int s0 = beg; s0 < end; s0 += 32) {
                 // which of the next 32 samples reach this block, in one step
                 const int my = s0 + lane;
-                int ru = 0, rv = 0;
                 bool rel = false;
+                int packed = 0;
                 if (my < end) {
                     const int d = __ldg(a.dd + my);
-                    ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
-                    rv = 4 * dbv - (d >> 2);
+                    const int ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
+                    const int rv = 4 * dbv - (d >> 2);
                     rel = ru < a.w && rv < a.w;
+                    packed = (ru + 3) | ((rv + 3) << 8);
                 }
-                const int packed = (ru + 3) | ((rv + 3) << 8);
-                unsigned mask = __ballot_sync(0xffffffffu, rel);
-                if (!mask) continue;
-                // software pipeline: the loads of the next relevant sample are
-                // in flight while the current one is accumulated
-                int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                int pk = __shfl_sync(0xffffffffu, packed, src);
-                long long sidx = s0 + src;
-                const float4 *rp = a.wrec + sidx * rq + 1;
-                float4 qx = __ldg(rp + (pk & 0xff));
-                float4 qy = __ldg(rp + (a.w + 3) + (pk >> 8));
-                float2 v = __ldg(sh + sidx * kKC);
-                while (true) {
-                    const float4 cx = qx, cy = qy;
-                    const float2 cv = v;
-                    const bool more = mask != 0;
-                    if (more) {
-                        src = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        pk = __shfl_sync(0xffffffffu, packed, src);
-                        sidx = s0 + src;
-                        rp = a.wrec + sidx * rq + 1;
-                        qx = __ldg(rp + (pk & 0xff));
-                        qy = __ldg(rp + (a.w + 3) + (pk >> 8));
-                        v = __ldg(sh + sidx * kKC);
-                    }
-                    const float wx[4] = {cx.x, cx.y, cx.z, cx.w};
-                    const float wy[4] = {cy.x, cy.y, cy.z, cy.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float2 t = make_float2(wy[j] * cv.x, wy[j] * cv.y);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            acc[j][i].x = fmaf(wx[i], t.x, acc[j][i].x);
-                            acc[j][i].y = fmaf(wx[i], t.y, acc[j][i].y);
-                        }
-                    }
-                    if (!more) break;
+                const unsigned mask = __ballot_sync(0xffffffffu, rel);
+                if (n + __popc(mask) > kListCap) {   // keep the list within its buffer
+                    __syncwarp();
+                    apply(n);
+                    n = 0;
+                    __syncwarp();
                 }
+                if (rel) list[n + __popc(mask & lt)] = make_int2(my, packed);
+                n += __popc(mask);
             }
         }
     }
+    __syncwarp();
+    apply(n);
     float2 *g = a.G + (long long)kc * a.mry * a.mrx * kKC;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -184,6 +221,7 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.wrec = reinterpret_cast<const float4 *>(w + p.off_wq);
     a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
     a.G = reinterpret_cast<float2 *>(w + p.off_G);
+    a.hdr = reinterpret_cast<const WsHeader *>(w);
     a.Lmax = p.L;
     a.mrx = p.mrx;
     a.mry = p.mry;
@@ -192,7 +230,7 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
-    const unsigned blocks = (unsigned)((p.mrx / 16) * (p.mry / 16) * p.n_kc);
+    const unsigned blocks = (unsigned)((p.mrx / 16) * (p.mry / 8) * p.n_kc);
     spread_kernel<<<blocks, kSpreadThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

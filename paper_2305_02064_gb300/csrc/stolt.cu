@@ -12,10 +12,11 @@
 // transformed by an inverse FFT and the Gaussian is deconvolved.
 //
 // One warp per column.  Because k_z grows with k, the samples of a column
-// are already sorted along the gridding axis, so each lane gathers one grid
-// point from the contiguous range of samples within reach (binary search)
-// -- no atomics, a fixed summation order.  The FFT then runs over the
-// 8 columns of the CTA in shared memory (fft.cuh).
+// are already sorted along the gridding axis: each lane spreads a contiguous
+// run of them into a small window of grid points kept in registers, and the
+// windows are then summed per grid point in lane order -- no atomics, a fixed
+// summation order.  The FFT then runs over the 8 columns of the CTA in shared
+// memory (fft.cuh).
 #include <cmath>
 
 #include "fft.cuh"
@@ -38,24 +39,24 @@ struct StoltArgs {
 
 constexpr int kStoltCols = 8;
 
-template <int MRZ>
+template <int MRZ, int WR>
 __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
     extern __shared__ float2 smem[];
-    float2 *grid = smem;                                  // [MRZ][8]
-    float2 *tw = grid + MRZ * kStoltCols;                 // [MRZ]
-    float2 *cbuf = tw + MRZ;                              // [8][nk]
+    constexpr int GP = fft_pitch(kStoltCols);            // padded row pitch of the grid tile
+    constexpr int WP = WR + 1;                            // padded pitch of a lane's window
+    float2 *grid = smem;                                  // [MRZ][GP]
+    float2 *tw = grid + MRZ * GP;                         // [MRZ]
+    float2 *winbuf = tw + MRZ;                            // [8 * 32][WP] per-lane register windows
+    float2 *cbuf = winbuf + kStoltCols * 32 * WP;         // [8][nk]
     float *tbuf = reinterpret_cast<float *>(cbuf + kStoltCols * a.nk);  // [8][nk]
-    float *kk = tbuf + kStoltCols * a.nk;                 // [nk]
+    int *jlo_s = reinterpret_cast<int *>(tbuf + kStoltCols * a.nk);   // [8 * 32]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncol = a.mx * a.my;
     const int col = blockIdx.x * kStoltCols + warp;
-    for (int e = tid; e < MRZ * kStoltCols; e += 256) grid[e] = make_float2(0.f, 0.f);
-    for (int k = tid; k < a.nk; k += 256) kk[k] = (float)(a.k0 + a.dk * k);
+    for (int e = tid; e < MRZ * GP; e += 256) grid[e] = make_float2(0.f, 0.f);
     fill_twiddles<MRZ, +1>(tw, tid, 256);
     __syncthreads();
     if (col < ncol) {
-        float2 *cw = cbuf + warp * a.nk;
-        float *tw_ = tbuf + warp * a.nk;
         const int om = col / a.my, on = col - (col / a.my) * a.my;
         const float kx = (float)((om - a.mx / 2) * a.kx_step);
         const float ky = (float)((on - a.my / 2) * a.ky_step);
@@ -64,59 +65,131 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
         const float turns_per_kz = (float)(zoff / (2.0 * kPi));
         const float cells_per_kz = (float)(a.dz * MRZ / (2.0 * kPi));
         const float2 *Sc = a.S + (long long)col * a.nkp;
-        int n_evan = 0;
+        const float hw = 0.5f * a.w;
+        // k = 2 pi f / c on the uniform grid, formed as k0_hi + (k0_lo + k dk)
+        // (k0 split into two floats): within half an ulp of the FP64 value
+        const float k0_hi = (float)a.k0, k0_lo = (float)(a.k0 - (double)k0_hi), dkf = (float)a.dk;
+        auto wavenumber = [&](int k) { return k0_hi + fmaf((float)k, dkf, k0_lo); };
+        // k_z grows with k: the evanescent samples (4k^2 <= k_x^2 + k_y^2) form a prefix
+        int kf = 0;
         for (int k0 = 0; k0 < a.nk; k0 += 32) {
             const int k = k0 + lane;
-            bool evan = false;
-            if (k < a.nk) {
-                const float kv = kk[k];
-                const float kz2 = 4.f * kv * kv - kr2;
-                float2 c = make_float2(0.f, 0.f);
-                float t = -1e30f;
-                if (kz2 > 0.f) {
-                    const float kz = sqrtf(kz2);
-                    t = kz * cells_per_kz;
-                    float ph = kz * turns_per_kz;
-                    ph -= rintf(ph);
-                    float sn, cs;
-                    sincospif(2.f * ph, &sn, &cs);
-                    const float2 s = __ldg(Sc + k);
-                    c = cmul(make_float2(s.x * kz, s.y * kz), make_float2(cs, sn));
-                } else {
-                    evan = true;
-                }
-                cw[k] = c;
-                tw_[k] = t;
-            }
-            n_evan += __popc(__ballot_sync(0xffffffffu, evan));
+            float kv = 0.f;
+            if (k < a.nk) kv = wavenumber(k);
+            const bool evan = k < a.nk && 4.f * kv * kv - kr2 <= 0.f;
+            kf += __popc(__ballot_sync(0xffffffffu, evan));
         }
-        __syncwarp();
-        const int kf = n_evan;   // k_z increases with k: evanescent samples form a prefix
+        // Eq. 14-15 for one sample: grid position t (cells) and weighted value c
+        auto sample = [&](int k, float &t, float2 &c) {
+            const float kv = wavenumber(k);
+            const float kz = sqrtf(4.f * kv * kv - kr2);
+            t = kz * cells_per_kz;
+            float ph = kz * turns_per_kz;
+            ph -= rintf(ph);                        // [-1/2, 1/2] turn
+            float sn, cs;
+            __sincosf(6.283185307179586f * ph, &sn, &cs);
+            const float2 sv = __ldg(Sc + k);
+            c = cmul(make_float2(sv.x * kz, sv.y * kz), make_float2(cs, sn));
+        };
         if (kf < a.nk) {
-            const float hw = 0.5f * a.w;
-            const int jlo = (int)ceilf(tw_[kf] - hw);
-            const int jhi = (int)ceilf(tw_[a.nk - 1] - hw) + a.w - 1;
-            for (int jb = jlo; jb <= jhi; jb += 32) {
-                const int j = jb + lane;
-                if (j <= jhi) {
-                    const float lo_t = (float)j - hw, hi_t = (float)j + hw;
-                    // first sample with t > lo_t
-                    int lo = kf, hi = a.nk;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (tw_[mid] > lo_t) hi = mid; else lo = mid + 1;
+            // Each lane spreads a contiguous run of samples (sorted along the
+            // gridding axis) into a window of WR grid points held in registers;
+            // the Gaussian weights of consecutive points follow the recurrence
+            // w_{i+1} = w_i r_i, r_{i+1} = r_i exp(-2 kappa).
+            const int nv = a.nk - kf;
+            const int per = (nv + 31) / 32;
+            const int k_beg = kf + lane * per, k_end = min(a.nk, k_beg + per);
+            const bool act = k_beg < k_end;
+            int jl = 0x7fffffff;
+            bool fits = true;
+            if (act) {
+                const float kv0 = wavenumber(k_beg), kv1 = wavenumber(k_end - 1);
+                const float t0 = sqrtf(4.f * kv0 * kv0 - kr2) * cells_per_kz;
+                const float t1 = sqrtf(4.f * kv1 * kv1 - kr2) * cells_per_kz;
+                jl = (int)ceilf(t0 - hw);
+                fits = (int)ceilf(t1 - hw) + a.w - 1 - jl + 1 <= WR;
+            }
+            if (__all_sync(0xffffffffu, fits)) {
+                float2 acc[WR];
+#pragma unroll
+                for (int i = 0; i < WR; ++i) acc[i] = make_float2(0.f, 0.f);
+                const float qk = __expf(-2.f * a.kappa);
+                for (int k = k_beg; k < k_end; ++k) {
+                    float t;
+                    float2 c;
+                    sample(k, t, c);
+                    const float d0 = t - (float)jl;
+                    float wgt = __expf(-a.kappa * d0 * d0);
+                    float rho = __expf(a.kappa * (2.f * d0 - 1.f));
+#pragma unroll
+                    for (int i = 0; i < WR; ++i) {
+                        acc[i].x = fmaf(wgt, c.x, acc[i].x);
+                        acc[i].y = fmaf(wgt, c.y, acc[i].y);
+                        wgt *= rho;
+                        rho *= qk;
                     }
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int k = lo; k < a.nk && tw_[k] <= hi_t; ++k) {
-                        const float d = tw_[k] - (float)j;
-                        const float wgt = __expf(-a.kappa * d * d);
-                        acc.x = fmaf(wgt, cw[k].x, acc.x);
-                        acc.y = fmaf(wgt, cw[k].y, acc.y);
+                }
+                float2 *mine = winbuf + (warp * 32 + lane) * WP;
+#pragma unroll
+                for (int i = 0; i < WR; ++i) mine[i] = acc[i];
+                jlo_s[warp * 32 + lane] = jl;
+                __syncwarp();
+                // sum the windows per grid point, lanes in a fixed order
+                const int nact = (nv + per - 1) / per;
+                const int *jw = jlo_s + warp * 32;
+                const float2 *wb = winbuf + warp * 32 * WP;
+                const int J_lo = jw[0], J_hi = jw[nact - 1] + WR - 1;
+                for (int jb = J_lo; jb <= J_hi; jb += 32) {
+                    const int j = jb + lane;
+                    if (j <= J_hi) {
+                        float2 sum = make_float2(0.f, 0.f);
+                        for (int l2 = 0; l2 < nact; ++l2) {
+                            const int o = j - jw[l2];
+                            if (o < 0) break;          // windows start in non-decreasing order
+                            if (o < WR) sum = cadd(sum, wb[l2 * WP + o]);
+                        }
+                        float2 &gref = grid[(j & (MRZ - 1)) * GP + warp];
+                        gref = cadd(gref, sum);
                     }
-                    float2 &gref = grid[(j & (MRZ - 1)) * kStoltCols + warp];
-                    gref = cadd(gref, acc);
+                    __syncwarp();
+                }
+            } else {
+                // a run that spans more than the register window (very coarse
+                // depth sampling): stage the samples and gather each grid
+                // point from the samples in reach, found by binary search
+                float2 *cw = cbuf + warp * a.nk;
+                float *tw_ = tbuf + warp * a.nk;
+                for (int k = kf + lane; k < a.nk; k += 32) {
+                    float t;
+                    float2 c;
+                    sample(k, t, c);
+                    cw[k] = c;
+                    tw_[k] = t;
                 }
                 __syncwarp();
+                const int jlo = (int)ceilf(tw_[kf] - hw);
+                const int jhi = (int)ceilf(tw_[a.nk - 1] - hw) + a.w - 1;
+                for (int jb = jlo; jb <= jhi; jb += 32) {
+                    const int j = jb + lane;
+                    if (j <= jhi) {
+                        const float lo_t = (float)j - hw, hi_t = (float)j + hw;
+                        int lo = kf, hi = a.nk;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (tw_[mid] > lo_t) hi = mid; else lo = mid + 1;
+                        }
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int k = lo; k < a.nk && tw_[k] <= hi_t; ++k) {
+                            const float d = tw_[k] - (float)j;
+                            const float wgt = __expf(-a.kappa * d * d);
+                            acc.x = fmaf(wgt, cw[k].x, acc.x);
+                            acc.y = fmaf(wgt, cw[k].y, acc.y);
+                        }
+                        float2 &gref = grid[(j & (MRZ - 1)) * GP + warp];
+                        gref = cadd(gref, acc);
+                    }
+                    __syncwarp();
+                }
             }
         }
     }
@@ -127,21 +200,31 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
         for (int q = lane; q < a.nz; q += 32) {
             const int qp = q - a.nz / 2;
             const float sc = a.deapod_scale * __expf((float)(qp * qp) * a.tau_z);
-            const float2 v = grid[(qp & (MRZ - 1)) * kStoltCols + warp];
+            const float2 v = grid[(qp & (MRZ - 1)) * GP + warp];
             Zc[q] = make_float2(v.x * sc, v.y * sc);
         }
     }
 }
 
-template <int MRZ>
-static cudaError_t launch_mrz(const StoltArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)(MRZ * kStoltCols + MRZ) * sizeof(float2) +
-                        (size_t)kStoltCols * a.nk * (sizeof(float2) + sizeof(float)) + (size_t)a.nk * sizeof(float);
-    cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ>, smem);
+template <int MRZ, int WR>
+static cudaError_t launch_mrz_wr(const StoltArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)(MRZ * fft_pitch(kStoltCols) + MRZ + kStoltCols * 32 * (WR + 1)) * sizeof(float2) +
+                        (size_t)kStoltCols * a.nk * (sizeof(float2) + sizeof(float)) +
+                        (size_t)kStoltCols * 32 * sizeof(int);
+    cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.mx * a.my + kStoltCols - 1) / kStoltCols);
-    stolt_kernel<MRZ><<<blocks, 256, smem, s>>>(a);
+    stolt_kernel<MRZ, WR><<<blocks, 256, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// register window: w + 2 grid points rounded up to an even count
+template <int MRZ>
+static cudaError_t launch_mrz(const StoltArgs &a, cudaStream_t s) {
+    if (a.w <= 6) return launch_mrz_wr<MRZ, 8>(a, s);
+    if (a.w <= 8) return launch_mrz_wr<MRZ, 10>(a, s);
+    if (a.w <= 10) return launch_mrz_wr<MRZ, 12>(a, s);
+    return launch_mrz_wr<MRZ, 14>(a, s);
 }
 
 cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
