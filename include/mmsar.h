@@ -141,6 +141,25 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
                          const double *pos, const double *tx, const double *rx,
                          void *vol, void *stream);
 
+/* One image request of a batch: its plan, its own workspace, inputs, output. */
+typedef struct {
+    mmsar_plan *plan;
+    void *workspace;
+    size_t workspace_bytes;
+    const void *echo;
+    const float *echo_scale;
+    const double *pos, *tx, *rx;
+    void *vol;
+} mmsar_request;
+
+/* Form n images of possibly different shapes (Sec. III imaging of several
+ * independent scans).  Request i runs on streams[i % n_streams] (cudaStream_t
+ * as void*), so uneven scans overlap on the device; ordering between the
+ * given streams is the caller's.  Each request needs its own workspace.
+ * Returns the first validation or launch error (requests before it were
+ * enqueued). */
+mmsar_status mmsar_image_batch(const mmsar_request *reqs, int n, void *const *streams, int n_streams);
+
 /* Read (and clear) the device error word of the last call that used this
  * workspace: synchronises `stream`, returns MMSAR_OK or the first device-side
  * condition (MMSAR_ERR_NONFINITE, MMSAR_ERR_INVALID_ARG for Z_c <= 0). */
@@ -171,6 +190,17 @@ size_t mmsar_static_workspace_bytes(void);
 mmsar_status mmsar_image_static(mmsar_plan *plan, const void *echo, const float *echo_scale,
                                 const double *pos, const double *tx, const double *rx,
                                 void *vol, void *stream);
+
+/* Reduced-precision echo storage (a storage choice of this library; the
+ * paper keeps full precision).  Converts the complex64 echo echo_c64 (device,
+ * n_complex values, 16-byte aligned) into interleaved FP16 or BF16 pairs in
+ * `out` (device, 4 * n_complex bytes) and writes the per-scan scale to
+ * `scale` (device float): scale = max(|Re|, |Im|) / 16384 (1 for an all-zero
+ * echo), out = round(echo / scale).  Pass `out` and `scale` to mmsar_image on
+ * a plan with the matching dtype; the arithmetic there is FP32.  `scratch` is
+ * one device int (overwritten).  Stream-ordered. */
+mmsar_status mmsar_quantize_echo(const void *echo_c64, int64_t n_complex, mmsar_echo_dtype dtype,
+                                 void *out, float *scale, int *scratch, void *stream);
 
 /* Thread-local text of the last error returned on this thread. */
 const char *mmsar_last_error(void);

@@ -18,7 +18,7 @@ import math
 from . import _lib
 from ._lib import MmsarError, library_path  # noqa: F401
 
-__all__ = ["Plan", "MmsarError", "peak", "library_path", "version"]
+__all__ = ["Plan", "MmsarError", "peak", "quantize_echo", "library_path", "version"]
 
 
 def version() -> str:
@@ -159,3 +159,25 @@ def peak(vol, scratch=None, stream=None):
     idx = int(r[0])
     mag = float(r[1:2].view(torch.float32)[0])
     return idx, mag
+
+
+def quantize_echo(echo, dtype="f16", out=None, scale=None, scratch=None, stream=None):
+    """Per-scan max-abs scaling of a complex64 CUDA echo into FP16 or BF16
+    pairs on the device.  Returns (out, scale): out has the echo's shape plus
+    a trailing axis of 2 (re, im); scale is a 1-element float32 tensor."""
+    import torch
+    lib = _lib.load()
+    if echo.dtype != torch.complex64:
+        raise ValueError("echo must be complex64")
+    want = torch.float16 if dtype == "f16" else torch.bfloat16
+    dev = echo.device
+    if out is None:
+        out = torch.empty(tuple(echo.shape) + (2,), dtype=want, device=dev)
+    if scale is None:
+        scale = torch.empty(1, dtype=torch.float32, device=dev)
+    if scratch is None:
+        scratch = torch.empty(1, dtype=torch.int32, device=dev)
+    _lib.check(lib.mmsar_quantize_echo(_ptr(echo, "echo"), ctypes.c_int64(echo.numel()), _lib.DTYPES[dtype],
+                                       _ptr(out, "out", want, 2 * echo.numel()), _ptr(scale, "scale", torch.float32, 1),
+                                       _ptr(scratch, "scratch", torch.int32, 1), _stream_handle(stream)))
+    return out, scale

@@ -26,13 +26,20 @@ DTYPES = {"c64": 0, "f16": 1, "bf16": 2}
 EXPORTS = ["mmsar_options_default", "mmsar_plan_create", "mmsar_plan_workspace_bytes", "mmsar_plan_info",
            "mmsar_stage_count", "mmsar_stage_name", "mmsar_plan_set_stage_events",
            "mmsar_image", "mmsar_poll_error", "mmsar_peak_scratch_bytes", "mmsar_peak", "mmsar_last_error",
-           "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static"]
+           "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static",
+           "mmsar_quantize_echo", "mmsar_image_batch"]
 
 
 class MmsarError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("echo", ctypes.c_void_p), ("echo_scale", ctypes.c_void_p), ("pos", ctypes.c_void_p),
+                ("tx", ctypes.c_void_p), ("rx", ctypes.c_void_p), ("vol", ctypes.c_void_p)]
 
 
 class Shape(ctypes.Structure):
@@ -100,6 +107,10 @@ def load(build_if_missing: bool = True):
         lib.mmsar_static_workspace_bytes.restype = sz
         lib.mmsar_image_static.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         lib.mmsar_image_static.restype = ctypes.c_int
+        lib.mmsar_quantize_echo.argtypes = [vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp]
+        lib.mmsar_quantize_echo.restype = ctypes.c_int
+        lib.mmsar_image_batch.argtypes = [ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int]
+        lib.mmsar_image_batch.restype = ctypes.c_int
         lib.mmsar_version.argtypes = []
         lib.mmsar_version.restype = ctypes.c_char_p
         _LIB = lib

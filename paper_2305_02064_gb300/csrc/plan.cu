@@ -300,6 +300,18 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     return MMSAR_OK;
 }
 
+mmsar_status mmsar_image_batch(const mmsar_request *reqs, int n, void *const *streams, int n_streams) {
+    if (n < 0 || (n > 0 && !reqs) || n_streams < 1 || !streams)
+        return fail(MMSAR_ERR_INVALID_ARG, "bad arguments to mmsar_image_batch");
+    for (int i = 0; i < n; ++i) {
+        const mmsar_request &r = reqs[i];
+        const mmsar_status st = mmsar_image(r.plan, r.workspace, r.workspace_bytes, r.echo, r.echo_scale, r.pos, r.tx,
+                                            r.rx, r.vol, streams[i % n_streams]);
+        if (st != MMSAR_OK) return st;
+    }
+    return MMSAR_OK;
+}
+
 mmsar_status mmsar_poll_error(const void *workspace, void *stream) {
     if (!workspace) return fail(MMSAR_ERR_INVALID_ARG, "null workspace");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

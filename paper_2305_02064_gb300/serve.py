@@ -1,0 +1,169 @@
+"""Continuous-batching server for imaging requests.
+
+Requests (scans of different sizes) arrive over time.  The scheduler admits a
+waiting request as soon as a stream slot is free and the device memory it
+needs fits under the admission cap together with everything already
+admitted; admitted requests run concurrently on their own streams, so work
+that arrives while others are on the GPU overlaps with them.  Each request's
+latency runs from its arrival to the completion of its volume.
+
+The scheduling logic (``Scheduler``) is independent of CUDA: it drives an
+executor object with ``start(req) -> handle``, ``done(handle) -> bool`` and
+``finish(handle)``; ``GpuExecutor`` is the CUDA one (pinned host echo ->
+device on the request's stream, FP16/BF16 quantisation with a per-scan scale,
+imaging, completion event).  Tests drive the scheduler with a fake executor.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+
+@dataclasses.dataclass
+class ServeRequest:
+    rid: int
+    scan: object
+    arrival: float              # seconds since the start of the run
+    footprint: int = 0          # device bytes while admitted
+    admitted: float = math.nan
+    completed: float = math.nan
+    result: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.completed - self.arrival
+
+
+class Scheduler:
+    """Admission by memory and slots, FIFO among arrived requests."""
+
+    def __init__(self, executor, slots: int, mem_cap: int, clock=time.perf_counter):
+        self.ex = executor
+        self.slots = slots
+        self.mem_cap = mem_cap
+        self.clock = clock
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.running = []            # (req, handle)
+        self.max_concurrent = 0
+
+    def run(self, requests, poll_sleep=0.0):
+        """Serve ``requests`` (sorted by arrival); returns them with times set."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()
+        done = []
+        t0 = self.clock()
+        for r in pending:
+            if r.footprint > self.mem_cap:
+                raise ValueError(f"request {r.rid} needs {r.footprint} bytes, above the admission cap")
+        while pending or waiting or self.running:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            # retire finished work first: it frees slots and memory
+            still = []
+            for req, h in self.running:
+                if self.ex.done(h):
+                    self.ex.finish(h)
+                    req.completed = self.clock() - t0
+                    self.in_use -= req.footprint
+                    done.append(req)
+                else:
+                    still.append((req, h))
+            self.running = still
+            # admit in arrival order while a slot and the memory allow
+            while waiting and len(self.running) < self.slots and \
+                    self.in_use + waiting[0].footprint <= self.mem_cap:
+                req = waiting.popleft()
+                req.admitted = self.clock() - t0
+                self.in_use += req.footprint
+                self.peak_in_use = max(self.peak_in_use, self.in_use)
+                self.running.append((req, self.ex.start(req)))
+                self.max_concurrent = max(self.max_concurrent, len(self.running))
+            if not self.running and not waiting and pending:
+                # idle until the next arrival
+                delay = pending[0].arrival - (self.clock() - t0)
+                if delay > 0:
+                    time.sleep(min(delay, 0.01))
+            elif poll_sleep:
+                time.sleep(poll_sleep)
+        return done
+
+
+def poisson_arrivals(n, rate_hz, seed=0):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
+
+
+def latency_summary(reqs):
+    import numpy as np
+    lat = np.array([r.latency for r in reqs])
+    span = max(r.completed for r in reqs) - min(r.arrival for r in reqs)
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "images_per_s": len(reqs) / span, "n": len(reqs)}
+
+
+class GpuExecutor:
+    """CUDA executor: one stream per running request, pinned host echoes."""
+
+    def __init__(self, device, dtype="f16", n_streams=8, keep_results=False):
+        import torch
+        self.dev = torch.device(device)
+        self.dtype = dtype
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(n_streams)]
+        self.free_streams = list(range(n_streams))
+        self.keep = keep_results
+        self._pinned = {}
+
+    def footprint(self, scan):
+        from .batch import plan_for
+        p = plan_for(scan, dtype=self.dtype)
+        T, R, P, Nk = scan.echo.shape
+        echo_dev = T * R * P * Nk * (8 if self.dtype == "c64" else 4)
+        staging = T * R * P * Nk * 8 if self.dtype != "c64" else 0
+        g = scan.grid
+        return int(p.workspace_bytes + echo_dev + staging + 8 * g.nx * g.ny * g.nz + 48 * (P + T + R))
+
+    def pin(self, req):
+        import numpy as np
+        import torch
+        s = req.scan
+        self._pinned[req.rid] = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                                 for a in (s.echo, np.asarray(s.pos, np.float64), np.asarray(s.tx, np.float64),
+                                           np.asarray(s.rx, np.float64))]
+
+    def start(self, req):
+        import torch
+        from . import quantize_echo
+        from .batch import plan_for
+        si = self.free_streams.pop()
+        st = self.streams[si]
+        plan = plan_for(req.scan, dtype=self.dtype)
+        if req.rid not in self._pinned:
+            self.pin(req)
+        echo_h, pos_h, tx_h, rx_h = self._pinned[req.rid]
+        with torch.cuda.stream(st):
+            echo = echo_h.to(self.dev, non_blocking=True)
+            pos, tx, rx = (t.to(self.dev, non_blocking=True) for t in (pos_h, tx_h, rx_h))
+            scale = None
+            if self.dtype != "c64":
+                echo, scale = quantize_echo(echo, self.dtype, stream=st)
+            ws = plan.new_workspace(self.dev)
+            vol = plan.new_volume(self.dev)
+            plan.image(ws, echo, pos, tx, rx, vol, echo_scale=scale, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return {"req": req, "si": si, "ev": ev, "bufs": (echo, pos, tx, rx, ws, scale), "vol": vol, "plan": plan}
+
+    def done(self, h):
+        return h["ev"].query()
+
+    def finish(self, h):
+        h["plan"].poll_error(h["bufs"][4], stream=self.streams[h["si"]])
+        if self.keep:
+            h["req"].result = h["vol"].cpu()
+        self.free_streams.append(h["si"])
+        h.clear()

@@ -1,0 +1,90 @@
+"""Batched and served imaging on the GPU: the same volume alone, in a batch,
+from a replayed CUDA graph and from the continuous-batching server."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rma
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def small_mix(n=6):
+    """Uneven scans shaped like the batched mix, scaled down for the test."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(100 + i)
+        npx, npy = int(rng.choice([6, 8, 10, 12])), int(rng.choice([6, 9, 12]))
+        nk = int(rng.choice([16, 32, 48]))
+        nx = 1 << int(np.ceil(np.log2(2 * npx + 8)))
+        out.append(synth.custom(nx_pos=npx, ny_pos=npy, nk=nk, layout="awr1443", nx=nx, ny=nx, nz=8 + 2 * i,
+                                seed=100 + i, serp=True, jitter=(1e-3, 2e-3), n_points=3))
+    return out
+
+
+def test_batch_equals_single(dev):
+    from paper_2305_02064_gb300.batch import ScanJob, image_batch
+    scans = small_mix()
+    single = []
+    for s in scans:
+        j = ScanJob(s, dev)
+        j.image()
+        single.append(j.vol.cpu().numpy())
+    jobs = [ScanJob(s, dev) for s in scans]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+    for st in streams:
+        st.wait_stream(torch.cuda.current_stream())
+    image_batch(jobs, streams)
+    torch.cuda.synchronize()
+    for j, ref, s in zip(jobs, single, scans):
+        got = j.vol.cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+        assert rma.nmse(got, rma.rma_exact(rma.setup_from(s))) <= 2e-5
+
+
+def test_graph_replay_equals_eager(dev):
+    from paper_2305_02064_gb300.batch import BatchGraph, ScanJob
+    scans = small_mix(4)
+    jobs = [ScanJob(s, dev) for s in scans]
+    g = BatchGraph(jobs, n_streams=2)
+    eager = [j.vol.clone() for j in jobs]
+    for j in jobs:
+        j.vol.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    for j, e in zip(jobs, eager):
+        assert torch.equal(j.vol.view(torch.float32), e.view(torch.float32))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "f16"])
+def test_server_alone_and_in_the_mix(dev, dtype):
+    from paper_2305_02064_gb300.serve import GpuExecutor, Scheduler, ServeRequest, latency_summary
+    scans = small_mix(8)
+    ex_alone = GpuExecutor(dev, dtype=dtype, n_streams=1, keep_results=True)
+    alone = {}
+    for i, s in enumerate(scans):
+        r = ServeRequest(i, s, 0.0, footprint=ex_alone.footprint(s))
+        Scheduler(ex_alone, slots=1, mem_cap=1 << 40).run([r])
+        alone[i] = r.result.numpy()
+    ex = GpuExecutor(dev, dtype=dtype, n_streams=4, keep_results=True)
+    reqs = [ServeRequest(i, s, 0.002 * i, footprint=ex.footprint(s)) for i, s in enumerate(scans)]
+    for r in reqs:
+        ex.pin(r)
+    cap = 3 * max(r.footprint for r in reqs)
+    sch = Scheduler(ex, slots=4, mem_cap=cap)
+    done = sch.run(reqs)
+    assert len(done) == len(scans) and sch.peak_in_use <= cap
+    for r in done:
+        assert np.array_equal(r.result.numpy().view(np.uint32), alone[r.rid].view(np.uint32))
+        if dtype == "c64":
+            assert rma.nmse(r.result.numpy(), rma.rma_exact(rma.setup_from(scans[r.rid]))) <= 2e-5
+    s = latency_summary(done)
+    assert s["p99_ms"] >= s["p50_ms"] > 0

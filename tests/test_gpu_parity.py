@@ -212,3 +212,34 @@ def test_kernel_widths(dev, tiny_scan, tol, w, bound):
     e = rma.nmse(got, ref)
     assert e <= bound, e
     assert rma.peak_index(got) == rma.peak_index(ref)
+
+
+@pytest.mark.parametrize("dtype,vs_fp32", [("f16", 1e-6), ("bf16", 2e-5)])
+def test_reduced_precision_storage(dev, dtype, vs_fp32):
+    """Echo stored as FP16/BF16 with a per-scan max-abs scale, FP32 arithmetic:
+    the storage rounding (unit roundoff 2^-11 / 2^-8) adds ~1e-7 / ~1e-6 of
+    NMSE; the result stays within the contract against the FP64 oracle."""
+    from paper_2305_02064_gb300 import Plan, quantize_echo
+    scan = synth.custom(nx_pos=12, ny_pos=10, nk=48, layout="awr1443", nx=32, ny=32, nz=12, seed=31, snr_db=30)
+    fp32, _ = run_gpu(scan, dev)
+    plan = Plan.for_scan(scan, dtype=dtype)
+    echo = torch.from_numpy(np.ascontiguousarray(scan.echo)).to(dev)
+    q, scale = quantize_echo(echo, dtype)
+    assert float(scale) == pytest.approx(np.abs(np.stack([scan.echo.real, scan.echo.imag])).max() / 16384, rel=1e-6)
+    back = (q.float() * scale).cpu().numpy()
+    rel = np.linalg.norm((back[..., 0] + 1j * back[..., 1]) - scan.echo) / np.linalg.norm(scan.echo)
+    assert rel < (5e-4 if dtype == "f16" else 4e-3)
+    ws, vol = plan.new_workspace(dev), plan.new_volume(dev)
+    args = [torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev) for a in (scan.pos, scan.tx, scan.rx)]
+    plan.image(ws, q, *args, vol, echo_scale=scale)
+    plan.poll_error(ws)
+    got = vol.cpu().numpy()
+    assert rma.nmse(got, fp32) <= vs_fp32
+    assert_parity(got, oracle_of(scan), plan.kernel_width)
+
+
+def test_quantize_zero_echo(dev):
+    from paper_2305_02064_gb300 import quantize_echo
+    z = torch.zeros(3, 5, dtype=torch.complex64, device=dev)
+    q, scale = quantize_echo(z, "f16")
+    assert float(scale) == 1.0 and torch.all(q == 0)
