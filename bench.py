@@ -48,7 +48,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["realistic", "tiny", "large"], default="realistic")
+    ap.add_argument("--workload", choices=["realistic", "tiny", "large", "batch", "serve"], default="realistic")
+    ap.add_argument("--mix", type=int, default=64, help="scans in the batched mix")
+    ap.add_argument("--requests", type=int, default=256, help="requests in the serving run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     return ap.parse_args()
@@ -190,25 +192,49 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- roofline model
+def occupied_window(plan, scan):
+    """Cells of the 2Mx x 2My gridding grid that can be nonzero (the same rule
+    the library applies on the device): the span of the samples' first taps
+    plus the kernel width, capped at the grid size."""
+    import numpy as np
+    pos, tx, rx = (np.asarray(a, np.float64).reshape(-1, 3) for a in (scan.pos, scan.tx, scan.rx))
+    if pos.shape[0] == 0:
+        return 0, 0
+    T = pos[None, None] + tx[:, None, None]
+    R = pos[None, None] + rx[None, :, None]
+    xv = 0.5 * (T[..., 0] + R[..., 0])
+    yv = 0.5 * (T[..., 1] + R[..., 1])
+    g = scan.grid
+    xc, yc = g.x0 + (g.nx // 2) * g.dx, g.y0 + (g.ny // 2) * g.dy
+    w = plan.kernel_width
+    u0 = np.ceil(2 * (xv - xc) / g.dx - w / 2)
+    v0 = np.ceil(2 * (yv - yc) / g.dy - w / 2)
+    ul = min(2 * plan.mx, int(u0.max() - u0.min()) + w)
+    vl = min(2 * plan.my, int(v0.max() - v0.min()) + w)
+    return ul, vl
+
+
 def stage_bytes(plan, scan):
-    """Algorithmic HBM bytes of each stage (compulsory reads + writes of the
-    data it transforms; see the design doc for the derivation)."""
+    """Algorithmic HBM bytes of each stage: the compulsory reads and writes of
+    the data it transforms, counting only the occupied window of the
+    gridding grid (the rest is known zero and never touched)."""
     T, R, P, Nk = scan.echo.shape
     L = T * R * P
     nkp = ((Nk + 31) // 32) * 32
     mx, my = plan.mx, plan.my
-    mrx, mry = 2 * mx, 2 * my
+    ul, vl = occupied_window(plan, scan)
     nx, ny, nz = scan.grid.nx, scan.grid.ny, scan.grid.nz
     c = 8  # complex64
     echo = L * Nk * c
     shat = L * nkp * c
-    G = mry * mrx * nkp * c
-    A = mry * mx * nkp * c
+    G = vl * ul * nkp * c          # occupied cells of the gridding grid
+    A = vl * mx * nkp * c          # occupied rows after the FFT along x'
     S = mx * my * nkp * c
     Z = mx * my * nz * c
     B = mx * ny * nz * c
     V = nx * ny * nz * c
-    return {"prep": L * 60 + 24 * P, "compensate": echo + shat + L * 12, "grid": shat + G + L * 16,
+    rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 4
+    return {"prep": L * (60 + rec) + 24 * P, "compensate": echo + shat + L * 12, "grid": shat + G + L * rec,
             "fft_x": G + A, "fft_y": A + S, "stolt": S + Z, "ifft_y": Z + B, "ifft_x": B + V}
 
 
@@ -366,7 +392,7 @@ def cpu_baseline(scan, vol_gpu):
     return ({"value": scan.grid.n_voxels / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
              "sample": "one whole scan of the workload through oracle.rma.rma_fast (FP64 Gaussian gridding w=16, "
                        "OpenMP + scipy.fft workers on all cores)", "seconds": dt},
-            {"nmse_vs_oracle": rma.nmse(got, ref), "peak_match": rma.peak_index(got) == rma.peak_index(ref)})
+            {"nmse_vs_oracle": float(rma.nmse(got, ref)), "peak_match": rma.peak_index(got) == rma.peak_index(ref)})
 
 
 # ----------------------------------------------------------------------------- reference (oracle) arm
@@ -398,6 +424,124 @@ def run_reference(args, dist):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------- batched mix
+def run_batch(args, dist):
+    """Batched uneven mix: the same 64 scans imaged (a) one after another on
+    one stream, (b) round-robin over 4 streams through mmsar_image_batch, and
+    (c) as one replayed CUDA graph of (b).  A step is the whole mix."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2305_02064_gb300.batch import BatchGraph, ScanJob, image_batch
+
+    dev = torch.device(f"cuda:{dist.local_rank}")
+    torch.cuda.set_device(dev)
+    scans = synth.batch_mix(args.mix, seed0=3000 + 1000 * dist.rank)
+    jobs = [ScanJob(s, dev) for s in scans]
+    voxels = sum(s.grid.n_voxels for s in scans)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(4)]
+    main_s = torch.cuda.Stream(device=dev)
+
+    def seq():
+        for j in jobs:
+            j.image(stream=main_s)
+
+    def multi():
+        cur = main_s
+        for st in streams:
+            st.wait_stream(cur)
+        image_batch(jobs, streams)
+        for st in streams:
+            cur.wait_stream(st)
+
+    graph = BatchGraph(jobs, n_streams=4, device=dev)
+
+    def timed(fn, steps):
+        with torch.cuda.stream(main_s):
+            for _ in range(args.warmup):
+                fn()
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(main_s):
+            e0.record(main_s)
+            for _ in range(steps):
+                fn()
+            e1.record(main_s)
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        return dist.max(e0.elapsed_time(e1) / steps)
+
+    steps = max(1, args.steps // 20)
+    ms = {"sequential": timed(seq, steps), "streams4": timed(multi, steps), "graph": timed(graph.replay, steps)}
+    best = ms["graph"]
+    n_img = len(jobs) * dist.world
+    return {"metric": "images/s, batched uneven mix (64 scans, 32x32..128x160 positions, Nk 64-256)",
+            "value": n_img / (best * 1e-3), "unit": "images/s", "n_gpus": dist.world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": best, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32", "data": "synthetic (seeded batched mix)",
+            "config": {"workload": f"batched uneven mix of {len(jobs)} scans (one CUDA graph, 4 streams)",
+                       "voxels_per_step": voxels * dist.world, "l2": "inputs larger than L2 (no flush)"},
+            "modes_ms_per_mix": ms,
+            "modes_images_per_s": {k: n_img / (v * 1e-3) for k, v in ms.items()},
+            "voxels_per_s": voxels * dist.world / (best * 1e-3),
+            "gpu_launches": sum(j.plan.kernels_per_image for j in jobs) * steps}
+
+
+# ----------------------------------------------------------------------------- serving
+def run_serve(args, dist):
+    """Poisson arrivals (200 req/s) of scans from the batched mix.  The
+    served form stores echoes as FP16 with a per-scan scale and admits up to
+    8 concurrent requests under a 40 GB device cap; the plain form images one
+    FP32 request at a time.  Latency = arrival -> volume ready."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2305_02064_gb300.serve import (GpuExecutor, Scheduler, ServeRequest, latency_summary,
+                                              poisson_arrivals)
+    from oracle import rma
+
+    dev = torch.device(f"cuda:{dist.local_rank}")
+    torch.cuda.set_device(dev)
+    pool = synth.batch_mix(16, seed0=4000 + 1000 * dist.rank)
+    rng = np.random.default_rng(7 + dist.rank)
+    picks = rng.integers(0, len(pool), args.requests)
+    arrivals = poisson_arrivals(args.requests, 200.0, seed=11 + dist.rank)
+    out = {}
+    results = {}
+    for name, dtype, slots in (("served_f16", "f16", 8), ("plain_fp32", "c64", 1)):
+        ex = GpuExecutor(dev, dtype=dtype, n_streams=slots, keep_results=True)
+        # warm every shape once (plans, kernel attributes, allocator)
+        for i in range(len(pool)):
+            r = ServeRequest(-1 - i, pool[i], 0.0, footprint=ex.footprint(pool[i]))
+            Scheduler(ex, slots=1, mem_cap=1 << 40).run([r])
+        reqs = [ServeRequest(i, pool[picks[i]], float(arrivals[i]), 0) for i in range(args.requests)]
+        for r in reqs:
+            r.footprint = ex.footprint(r.scan)
+            ex.pin(r)
+        torch.cuda.synchronize(dev)
+        dist.barrier()
+        sch = Scheduler(ex, slots=slots, mem_cap=40 << 30)
+        done = sch.run(reqs)
+        out[name] = latency_summary(done)
+        out[name]["max_concurrent"] = sch.max_concurrent
+        out[name]["peak_admitted_gb"] = sch.peak_in_use / 2 ** 30
+        results[name] = {r.rid: r.result for r in done}
+    # accuracy of the served form against the plain FP32 form, per request
+    worst = float(max(rma.nmse(results["served_f16"][i].numpy(), results["plain_fp32"][i].numpy())
+                      for i in range(args.requests)))
+    s = out["served_f16"]
+    return {"metric": "images/s with p50/p99 latency, served Poisson stream (200 req/s) from the batched mix",
+            "value": s["images_per_s"] * dist.world, "unit": "images/s", "n_gpus": dist.world,
+            "steps": args.requests, "warmup": len(pool), "ms_per_step": 1e3 / s["images_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp16 storage, fp32 arithmetic", "data": "synthetic (seeded batched mix)",
+            "config": {"workload": "serving: Poisson 200 req/s, continuous batching (8 slots), 40 GB admission cap",
+                       "requests": args.requests},
+            "latency_ms": {"p50": s["p50_ms"], "p99": s["p99_ms"]},
+            "forms": out, "worst_nmse_served_vs_plain_fp32": worst}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -408,6 +552,12 @@ def main():
         dist.close()
         return 0
     dist = Dist(want_cuda=True)
+    if args.workload in ("batch", "serve"):
+        res = (run_batch if args.workload == "batch" else run_serve)(args, dist)
+        if dist.rank == 0:
+            print(json.dumps(res))
+        dist.close()
+        return 0
     res, scan, vol = run_ours(args, dist)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cb, acc = cpu_baseline(scan, vol)
