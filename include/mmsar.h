@@ -141,6 +141,18 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
                          const double *pos, const double *tx, const double *rx,
                          void *vol, void *stream);
 
+/* Direct back-projection, the paper's reference algorithm (Sec. III, used
+ * for comparison in Sec. V):
+ *   o_BP(r) = sum_{t,r,p,k} s(t,r,p,k) exp(+j k (|T - r| + |R - r|)),
+ * k = 2 pi (f0 + k df) / c, unnormalised, at n_voxels voxel centres
+ * `voxels` (device double [n][3]) or, with voxels == NULL, at every voxel of
+ * the plan's grid (output in the mmsar_image layout).  out: device complex64
+ * [n].  Complex64 echoes only.  Cost: voxels x samples x frequencies; meant
+ * for cross-checks and small grids.  Stream-ordered. */
+mmsar_status mmsar_backproject(const mmsar_plan *plan, const void *echo, const double *pos,
+                               const double *tx, const double *rx, const double *voxels,
+                               int64_t n_voxels, void *out, void *stream);
+
 /* One image request of a batch: its plan, its own workspace, inputs, output. */
 typedef struct {
     mmsar_plan *plan;

@@ -141,6 +141,22 @@ class Plan:
         _lib.check(self._lib.mmsar_plan_set_stage_events(self._h, arr, len(events)))
         self._events = list(events)
 
+    def backproject(self, echo, pos, tx, rx, out=None, voxels=None, stream=None):
+        """Direct back-projection at ``voxels`` (device float64 [n, 3]) or at
+        every voxel of the plan's grid; returns complex64 [n] (or the grid)."""
+        import torch
+        s = self.shape
+        n = voxels.shape[0] if voxels is not None else self.grid.nx * self.grid.ny * self.grid.nz
+        if out is None:
+            shape = (n,) if voxels is not None else self.volume_shape
+            out = torch.empty(shape, dtype=torch.complex64, device=echo.device)
+        _lib.check(self._lib.mmsar_backproject(
+            self._h, _ptr(echo, "echo", torch.complex64, s.n_tx * s.n_rx * s.n_pos * s.n_k),
+            _ptr(pos, "pos", torch.float64, 3 * s.n_pos), _ptr(tx, "tx", torch.float64, 3 * s.n_tx),
+            _ptr(rx, "rx", torch.float64, 3 * s.n_rx), _ptr(voxels, "voxels", torch.float64),
+            ctypes.c_int64(n), _ptr(out, "out", torch.complex64, n), _stream_handle(stream)))
+        return out
+
     def poll_error(self, workspace, stream=None):
         _lib.check(self._lib.mmsar_poll_error(_ptr(workspace, "workspace"), _stream_handle(stream)))
 

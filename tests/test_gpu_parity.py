@@ -243,3 +243,12 @@ def test_quantize_zero_echo(dev):
     z = torch.zeros(3, 5, dtype=torch.complex64, device=dev)
     q, scale = quantize_echo(z, "f16")
     assert float(scale) == 1.0 and torch.all(q == 0)
+
+
+def test_single_plane_image(dev):
+    """nz = 1: the 2-D x-y image at one known depth (Sec. V, 2-D variant)."""
+    scan = synth.custom(nx_pos=14, ny_pos=12, nk=40, layout="awr1443", nx=32, ny=32, nz=1, z0=0.30, seed=17,
+                        scatterers=[[2e-3, -3e-3, 0.30, 1.0], [-6e-3, 5e-3, 0.30, 0.6]])
+    got, plan = run_gpu(scan, dev, z_scene=0.30)
+    assert got.shape == (32, 32, 1)
+    assert_parity(got, oracle_of(scan, z_scene=0.30), plan.kernel_width)
