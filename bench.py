@@ -105,12 +105,15 @@ class Dist:
 
 
 # ----------------------------------------------------------------------------- workloads
+LARGE_POINTS = 200   # scatterers of the large scene (echo synthesis cost grows with them; imaging does not)
+
+
 def make_scan(workload: str, rank: int):
     import synth
     if workload == "tiny":
         return synth.tiny(seed=rank)
     if workload == "large":
-        return synth.large(seed=5000 + rank)
+        return synth.large(seed=5000 + rank, n_points=LARGE_POINTS)
     return synth.realistic(seed=2000 + rank)
 
 
@@ -120,7 +123,8 @@ def workload_config(scan, workload, plan=None):
     cfg = {"workload": {"tiny": "tiny: 1Tx x 2Rx, 16x16 jittered positions, Nk=32 -> 32x32x16",
                         "realistic": "realistic single scan: 2Tx x 4Rx, 128x128 random-walk serpentine, "
                                      "Nk=256 -> 256x256x64 complex64",
-                        "large": "large: 3Tx x 4Rx, 256x256 positions, Nk=512 -> 512x512x128"}[workload],
+                        "large": f"large: 3Tx x 4Rx, 256x256 positions, Nk=512 -> 512x512x128 "
+                                 f"({LARGE_POINTS} scatterers)"}[workload],
            "tx_rx_pos_k": [T, R, P, Nk], "voxels": [g.nx, g.ny, g.nz],
            "echo_bytes": int(scan.echo.nbytes), "l2": "inputs larger than L2 (no flush)"
            if scan.echo.nbytes > 129e6 else "L2 flushed between steps",
@@ -395,6 +399,49 @@ def cpu_baseline(scan, vol_gpu):
             {"nmse_vs_oracle": float(rma.nmse(got, ref)), "peak_match": rma.peak_index(got) == rma.peak_index(ref)})
 
 
+def storage_comparison(scan, vol_fp32, args):
+    """BF16 and FP16 echo storage against FP32 storage and the FP64 oracle on
+    the same scan: per-image device time and NMSE (Gaussian gridding oracle,
+    w = 12, relative error ~1e-6 per transform)."""
+    import numpy as np
+    import torch
+    import paper_2305_02064_gb300 as mm
+    from oracle import rma
+    dev = vol_fp32.device
+    echo = torch.from_numpy(np.ascontiguousarray(scan.echo)).to(dev)
+    pos, tx, rx = (torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev) for a in (scan.pos, scan.tx, scan.rx))
+    out = {}
+    vols = {"fp32": vol_fp32.cpu().numpy()}
+    for dt in ("bf16", "f16"):
+        plan = mm.Plan.for_scan(scan, dtype=dt)
+        q, sc = mm.quantize_echo(echo, dt)
+        ws, vol = plan.new_workspace(dev), plan.new_volume(dev)
+        for _ in range(3):
+            plan.image(ws, q, pos, tx, rx, vol, echo_scale=sc)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n = max(3, args.steps // 10)
+        for _ in range(n):
+            plan.image(ws, q, pos, tx, rx, vol, echo_scale=sc)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        plan.poll_error(ws)
+        out[dt] = {"ms_per_image": e0.elapsed_time(e1) / n}
+        vols[dt] = vol.cpu().numpy()
+        del ws, q
+    t0 = time.time()
+    ref = rma.rma_fast(rma.setup_from(scan), w=12)
+    oracle_s = time.time() - t0
+    for k, v in vols.items():
+        out.setdefault(k, {})["nmse_vs_oracle"] = float(rma.nmse(v, ref))
+        out[k]["peak_match"] = rma.peak_index(v) == rma.peak_index(ref)
+    for k in ("bf16", "f16"):
+        out[k]["nmse_vs_fp32"] = float(rma.nmse(vols[k], vols["fp32"]))
+    out["oracle_seconds"] = oracle_s
+    return out
+
+
 # ----------------------------------------------------------------------------- reference (oracle) arm
 def run_reference(args, dist):
     from oracle import rma
@@ -559,6 +606,8 @@ def main():
         dist.close()
         return 0
     res, scan, vol = run_ours(args, dist)
+    if args.workload == "large" and dist.rank == 0 and dist.world == 1:
+        res["storage_comparison"] = storage_comparison(scan, vol, args)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cb, acc = cpu_baseline(scan, vol)
         res["cpu_baseline"] = cb

@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
         return so
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", src, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", src, "-o", tmp, "-lm"])
     os.replace(tmp, so)
     return so
 

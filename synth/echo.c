@@ -13,7 +13,8 @@
  *
  * The phase over the uniform frequency grid is generated by a complex
  * rotation recurrence that is re-anchored from an exact sincos every 32
- * steps, which keeps the FP64 phase error below 1e-13 rad.
+ * steps, which keeps the FP64 phase error below 1e-13 rad; scatterers are
+ * processed in blocks of 8 so that the per-frequency update vectorises.
  *
  * Layout: pos [P][3], tx [T][3], rx [R][3], scat [S][4] = (x, y, z, sigma),
  * out [T][R][P][Nk][2] float (interleaved re, im).  All metres / Hz.
@@ -47,29 +48,47 @@ int synth_echo(int T, int R, int P, int Nk,
             const double Ry = pos[3 * p + 1] + rx[3 * r + 1];
             const double Rz = pos[3 * p + 2] + rx[3 * r + 2];
             for (int k = 0; k < 2 * Nk; ++k) acc[k] = 0.0;
-            for (int s = 0; s < S; ++s) {
-                const double *q = scat + 4 * s;
-                const double dTx = Tx - q[0], dTy = Ty - q[1], dTz = Tz - q[2];
-                const double dRx = Rx - q[0], dRy = Ry - q[1], dRz = Rz - q[2];
-                const double RT = sqrt(dTx * dTx + dTy * dTy + dTz * dTz);
-                const double RR = sqrt(dRx * dRx + dRy * dRy + dRz * dRz);
-                const double Rrt = RT + RR;
-                const double amp = q[3] * (amplitude ? 1.0 / (RT * RR) : 1.0);
-                /* rotation by exp(-j * 2*pi*df/c * Rrt) per frequency step */
-                const double dphi = -two_pi * df / SYNTH_C0 * Rrt;
-                const double cr = cos(dphi), ci = sin(dphi);
-                double zr = 0.0, zi = 0.0;
-                for (int k = 0; k < Nk; ++k) {
-                    if ((k & 31) == 0) {
-                        const double phi = -two_pi * (f0 + df * k) / SYNTH_C0 * Rrt;
-                        zr = amp * cos(phi);
-                        zi = amp * sin(phi);
+            /* scatterers in blocks of SB so the per-frequency update runs
+             * across a block (vectorisable); the phase of each scatterer is
+             * re-anchored from an exact sincos every 32 frequencies */
+            enum { SB = 8 };
+            for (int s0 = 0; s0 < S; s0 += SB) {
+                const int nb = S - s0 < SB ? S - s0 : SB;
+                double Rrt[SB], amp[SB], cr[SB], ci[SB], zr[SB], zi[SB];
+                for (int j = 0; j < SB; ++j) {
+                    Rrt[j] = 0.0; amp[j] = 0.0; cr[j] = 1.0; ci[j] = 0.0; zr[j] = 0.0; zi[j] = 0.0;
+                    if (j >= nb) continue;
+                    const double *q = scat + 4 * (s0 + j);
+                    const double dTx = Tx - q[0], dTy = Ty - q[1], dTz = Tz - q[2];
+                    const double dRx = Rx - q[0], dRy = Ry - q[1], dRz = Rz - q[2];
+                    const double RT = sqrt(dTx * dTx + dTy * dTy + dTz * dTz);
+                    const double RR = sqrt(dRx * dRx + dRy * dRy + dRz * dRz);
+                    Rrt[j] = RT + RR;
+                    amp[j] = q[3] * (amplitude ? 1.0 / (RT * RR) : 1.0);
+                    /* rotation by exp(-j * 2*pi*df/c * Rrt) per frequency step */
+                    const double dphi = -two_pi * df / SYNTH_C0 * Rrt[j];
+                    cr[j] = cos(dphi);
+                    ci[j] = sin(dphi);
+                }
+                for (int k0 = 0; k0 < Nk; k0 += 32) {
+                    for (int j = 0; j < nb; ++j) {
+                        const double phi = -two_pi * (f0 + df * k0) / SYNTH_C0 * Rrt[j];
+                        zr[j] = amp[j] * cos(phi);
+                        zi[j] = amp[j] * sin(phi);
                     }
-                    acc[2 * k] += zr;
-                    acc[2 * k + 1] += zi;
-                    const double nr = zr * cr - zi * ci;
-                    zi = zr * ci + zi * cr;
-                    zr = nr;
+                    const int k1 = k0 + 32 < Nk ? k0 + 32 : Nk;
+                    for (int k = k0; k < k1; ++k) {
+                        double sr = 0.0, si = 0.0;
+                        for (int j = 0; j < SB; ++j) {
+                            sr += zr[j];
+                            si += zi[j];
+                            const double nr = zr[j] * cr[j] - zi[j] * ci[j];
+                            zi[j] = zr[j] * ci[j] + zi[j] * cr[j];
+                            zr[j] = nr;
+                        }
+                        acc[2 * k] += sr;
+                        acc[2 * k + 1] += si;
+                    }
                 }
             }
             float *o = out + (size_t)l * 2 * Nk;
