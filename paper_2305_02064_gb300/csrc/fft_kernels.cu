@@ -17,13 +17,32 @@ namespace mmsar {
 
 constexpr int kFftThreads = 256;
 
+// Columns per tile and row pitch: two tiles (double buffer) of L x P complex
+// fit in shared memory; P is even so 16-byte asynchronous copies stay aligned.
 __host__ __device__ constexpr int fft_cols(int L) { return L >= 256 ? 8192 / L : 32; }
+__host__ __device__ constexpr int fft_tile_pitch(int C) { return C >= 32 ? C : C + 2; }
 
-template <int L, int SIGN>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc, bool live, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    const int n = live ? bytes : 0;   // 0 source bytes: the destination is zero-filled
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// One tile per CTA: the tile arrives through asynchronous copies (zero-filled
+// outside the input window), is transformed in shared memory and the
+// selected rows are scaled and stored.  VEC complex values per copy (2 when
+// every row start is 16-byte aligned, else 1).
+template <int L, int SIGN, int VEC>
 __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     constexpr int C = fft_cols(L);
-    constexpr int P = fft_pitch(C);
-    extern __shared__ float2 smem[];
+    constexpr int P = fft_tile_pitch(C);
+    extern __shared__ __align__(16) float2 smem[];
     float2 *tile = smem;
     float2 *tw = smem + L * P;
     const int tid = threadIdx.x;
@@ -48,17 +67,20 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     const int cw = min(C, a.ncols - c0);
     const float2 *in = a.in + t1 * a.in_t1 + t2 * a.in_t2 + c0;
     float2 *out = a.out + t1 * a.out_t1 + t2 * a.out_t2 + c0;
-    fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
-    for (int e = tid; e < L * C; e += kFftThreads) {
-        const int f = e / C, c = e - (e / C) * C;
+    constexpr int PER_ROW = C / VEC;
+    for (int e = tid; e < L * PER_ROW; e += kFftThreads) {
+        const int f = e / PER_ROW, c = (e - f * PER_ROW) * VEC;
         const int r = (f - a.in_shift) & (L - 1);
         int d = r - wlo;
         if (d < 0) d += a.n_in;
         const bool live = r < a.n_in && c < cw && d < wlen;
-        tile[f * P + c] = live ? __ldg(in + (long long)r * a.in_row + c) : make_float2(0.f, 0.f);
+        cp_async(tile + f * P + c, live ? in + (long long)r * a.in_row + c : a.in, live, VEC * 8);
     }
+    cp_async_commit();
+    fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
+    cp_async_wait<0>();
     __syncthreads();
-    smem_fft<L, C, kFftThreads, SIGN>(tile, tw);
+    smem_fft<L, C, kFftThreads, SIGN, P>(tile, tw);
     const int half = a.n_out / 2;
     for (int e = tid; e < a.n_out * C; e += kFftThreads) {
         const int o = e / C, c = e - (e / C) * C;
@@ -72,16 +94,25 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     }
 }
 
-template <int L, int SIGN>
-static cudaError_t launch_L(const ColumnFFT &a, cudaStream_t s) {
+template <int L, int SIGN, int VEC>
+static cudaError_t launch_LV(const ColumnFFT &a, cudaStream_t s) {
     constexpr int C = fft_cols(L);
-    const size_t smem = (size_t)(L * fft_pitch(C) + L) * sizeof(float2);
-    cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN>, smem);
+    const size_t smem = (size_t)(L * fft_tile_pitch(C) + L) * sizeof(float2);
+    cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN, VEC>, smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (a.ncols + C - 1) / C;
     dim3 grid((unsigned)(a.nt2 * nchunks), (unsigned)a.nt1);
-    column_fft_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(a);
+    column_fft_kernel<L, SIGN, VEC><<<grid, kFftThreads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int L, int SIGN>
+static cudaError_t launch_L(const ColumnFFT &a, cudaStream_t s) {
+    // 16-byte copies need every row start (and the column chunk starts) on a
+    // 16-byte boundary
+    const bool even = (a.ncols % 2 == 0) && (a.in_row % 2 == 0) && (a.in_t1 % 2 == 0) && (a.in_t2 % 2 == 0) &&
+                      (reinterpret_cast<uintptr_t>(a.in) % 16 == 0);
+    return even ? launch_LV<L, SIGN, 2>(a, s) : launch_LV<L, SIGN, 1>(a, s);
 }
 
 template <int SIGN>

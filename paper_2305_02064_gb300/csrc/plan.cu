@@ -124,6 +124,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.nkp = p.n_kc * kKC;
     p.L = (int64_t)sh.n_tx * sh.n_rx * sh.n_pos;
     if (p.L > (int64_t)0x7fffffff / 2) return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "too many samples (%lld)", (long long)p.L);
+    if (p.L * (int64_t)(2 * p.w + 7) >= ((int64_t)1 << 31) || p.L * kKC >= ((int64_t)1 << 31))
+        return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "too many samples for 32-bit record indices (%lld)", (long long)p.L);
     p.nbx = p.mrx / kBin;
     p.nby = p.mry / kBin;
     p.n_bins = (int64_t)p.nbx * p.nby;

@@ -102,10 +102,11 @@ __device__ __forceinline__ bool tile_meets(int t0, int span, int lo, int len, in
 
 constexpr int kSpreadThreads = 256;   // 8 warps: a 16 x 8-cell tile
 
-constexpr int kListCap = 256;   // relevant samples listed per warp before they are applied
+constexpr int kListCap = 192;   // relevant samples listed per warp before they are applied
 
 __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a) {
-    __shared__ int2 lists[kSpreadThreads / 32][kListCap];   // (sample, quad offsets) per warp
+    // per warp: (x-quad index, y-quad index, sample index) of each listed sample
+    __shared__ int4 lists[kSpreadThreads / 32][kListCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx >> 4;
     // the frequency chunk varies fastest, so the chunks of one tile run
@@ -127,19 +128,18 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[j][i] = make_float2(0.f, 0.f);
     const float2 *sh = a.shat + (long long)kc * a.Lmax * kKC + lane;
-    int2 *list = lists[warp];
+    int4 *list = lists[warp];
 
-    // apply the listed samples; the loads of entry i + 2 are issued while
-    // entry i is accumulated
+    // apply the listed samples through a three-deep pipeline: the loads of
+    // entry i + 3 are issued as soon as entry i has been accumulated
     auto apply = [&](int n) {
-        float4 xA, yA, xB, yB;
-        float2 vA, vB;
+        float4 x0, y0, x1, y1, x2, y2;
+        float2 v0, v1, v2;
         auto fetch = [&](int i, float4 &x, float4 &y, float2 &v) {
-            const int2 e = list[i];
-            const float4 *rp = a.wrec + (long long)e.x * rq + 1;
-            x = __ldg(rp + (e.y & 0xff));
-            y = __ldg(rp + nq + (e.y >> 8));
-            v = __ldg(sh + (long long)e.x * kKC);
+            const int4 e = list[i];
+            x = __ldg(a.wrec + e.x);
+            y = __ldg(a.wrec + e.y);
+            v = __ldg(sh + (e.z << 5));
         };
         auto consume = [&](const float4 &x, const float4 &y, const float2 &v) {
             const float wx[4] = {x.x, x.y, x.z, x.w};
@@ -154,18 +154,18 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
                 }
             }
         };
-        if (n > 0) fetch(0, xA, yA, vA);
-        if (n > 1) fetch(1, xB, yB, vB);
-        for (int i = 0; i < n; i += 2) {
-            const float4 cx = xA, cy = yA;
-            const float2 cv = vA;
-            if (i + 2 < n) fetch(i + 2, xA, yA, vA);
-            consume(cx, cy, cv);
+        if (n > 0) fetch(0, x0, y0, v0);
+        if (n > 1) fetch(1, x1, y1, v1);
+        if (n > 2) fetch(2, x2, y2, v2);
+        for (int i = 0; i < n; i += 3) {
+            consume(x0, y0, v0);
+            if (i + 3 < n) fetch(i + 3, x0, y0, v0);
             if (i + 1 >= n) break;
-            const float4 dx = xB, dy = yB;
-            const float2 dv = vB;
-            if (i + 3 < n) fetch(i + 3, xB, yB, vB);
-            consume(dx, dy, dv);
+            consume(x1, y1, v1);
+            if (i + 4 < n) fetch(i + 4, x1, y1, v1);
+            if (i + 2 >= n) break;
+            consume(x2, y2, v2);
+            if (i + 5 < n) fetch(i + 5, x2, y2, v2);
         }
     };
 
@@ -184,13 +184,14 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
                 // which of the next 32 samples reach this block, in one step
                 const int my = s0 + lane;
                 bool rel = false;
-                int packed = 0;
+                int4 ent = make_int4(0, 0, 0, 0);
                 if (my < end) {
                     const int d = __ldg(a.dd + my);
                     const int ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
                     const int rv = 4 * dbv - (d >> 2);
                     rel = ru < a.w && rv < a.w;
-                    packed = (ru + 3) | ((rv + 3) << 8);
+                    const int base = my * rq + 1;         // the sample's x quads, then its y quads
+                    ent = make_int4(base + ru + 3, base + nq + rv + 3, my, 0);
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, rel);
                 if (n + __popc(mask) > kListCap) {   // keep the list within its buffer
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
                     n = 0;
                     __syncwarp();
                 }
-                if (rel) list[n + __popc(mask & lt)] = make_int2(my, packed);
+                if (rel) list[n + __popc(mask & lt)] = ent;
                 n += __popc(mask);
             }
         }
