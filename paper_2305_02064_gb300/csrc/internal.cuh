@@ -31,7 +31,9 @@ struct WsHeader {
     // occupied window of the periodic gridding grid: cells lo .. lo + len - 1
     // (mod the grid size) can be nonzero; everything else is known zero
     int u_lo, u_len, v_lo, v_len;
-    double pad[10];
+    int zref_done;      // blocks of the z_ref reduction that have finished
+    int pad_i;
+    double pad[9];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 
@@ -62,6 +64,8 @@ struct Plan {
     // workspace layout (byte offsets)
     size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm, off_srec;
     size_t off_dd, off_wq;   // per sorted sample: in-bin cell offsets; Gaussian weight quads
+    size_t off_partials;     // per-block sums of the z_ref reduction
+    size_t off_blocksum;     // per-block totals of the bin scan
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
     // optional per-stage timing events (caller-owned)
@@ -70,7 +74,7 @@ struct Plan {
 };
 
 constexpr int kStages = 8;
-constexpr int kKernelsPerImage = 13;
+constexpr int kKernelsPerImage = 14;
 
 }  // namespace mmsar
 

@@ -147,6 +147,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
         return at;
     };
     const size_t L = (size_t)p.L;
+    p.off_partials = take(sizeof(double) * 128);
+    p.off_blocksum = take(sizeof(int) * (size_t)((p.n_bins + 1023) / 1024));
     p.off_counts = take(sizeof(int) * (size_t)p.n_bins);
     p.off_offsets = take(sizeof(int) * ((size_t)p.n_bins + 1));
     p.off_cursor = take(sizeof(int) * (size_t)p.n_bins);

@@ -24,41 +24,64 @@
 namespace mmsar {
 
 // ------------------------------------------------------------------ z_ref
-__global__ void __launch_bounds__(1024) zref_kernel(const double *__restrict__ pos, int P,
-                                                    const double *__restrict__ tx, int T,
-                                                    const double *__restrict__ rx, int R, int given,
-                                                    double z_given, WsHeader *hdr) {
-    __shared__ double red[1024];
+// Mean of z_l = p_z + (tx_z + rx_z)/2 over all samples, i.e.
+// mean(p_z) + (mean(tx_z) + mean(rx_z))/2.  Every block sums a fixed slice of
+// the positions in a fixed order and the last block to finish adds the block
+// sums in index order, so the result is the same bits on every run.  Block 0
+// also resets the occupied-window accumulators of the header.
+constexpr int kZrefThreads = 256;
+constexpr int kZrefMaxBlocks = 128;
+
+__global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__restrict__ pos, int P,
+                                                            const double *__restrict__ tx, int T,
+                                                            const double *__restrict__ rx, int R, int given,
+                                                            double z_given, double *partials, WsHeader *hdr) {
+    __shared__ double red[kZrefThreads];
+    __shared__ bool last;
     const int tid = threadIdx.x;
-    if (tid == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         hdr->u_min = hdr->v_min = 0x7fffffff;
         hdr->u_max = hdr->v_max = -0x7fffffff - 1;
+        if (given) hdr->z_ref = z_given;
     }
-    if (given) {
-        if (tid == 0) hdr->z_ref = z_given;
-        return;
-    }
-    double s = 0.0;
-    for (int p = tid; p < P; p += 1024) s += pos[3 * p + 2];
-    red[tid] = s;
+    if (given) return;
+    const int per = (P + gridDim.x - 1) / gridDim.x;
+    const int p0 = blockIdx.x * per, p1 = min(P, p0 + per);
+    double acc = 0.0;
+    for (int p = p0 + tid; p < p1; p += kZrefThreads) acc += pos[3 * p + 2];
+    red[tid] = acc;
     __syncthreads();
-    for (int h = 512; h > 0; h >>= 1) {
+    for (int h = kZrefThreads / 2; h > 0; h >>= 1) {
         if (tid < h) red[tid] += red[tid + h];
         __syncthreads();
     }
     if (tid == 0) {
+        partials[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(&hdr->zref_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        double sum = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile double *)partials)[b];
         double st = 0.0, sr = 0.0;
         for (int t = 0; t < T; ++t) st += tx[3 * t + 2];
         for (int r = 0; r < R; ++r) sr += rx[3 * r + 2];
-        hdr->z_ref = (P > 0 ? red[0] / P : 0.0) + 0.5 * (st / T + sr / R);
+        hdr->z_ref = (P > 0 ? sum / P : 0.0) + 0.5 * (st / T + sr / R);
     }
 }
 
 cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
                         cudaStream_t s) {
-    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-    zref_kernel<<<1, p.zref_given ? 32 : 1024, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
-                                                       p.zref_given ? 1 : 0, p.z_ref, hdr);
+    char *w = reinterpret_cast<char *>(ws);
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
+    int blocks = (p.shape.n_pos + 2047) / 2048;
+    blocks = blocks < 1 ? 1 : (blocks > kZrefMaxBlocks ? kZrefMaxBlocks : blocks);
+    if (p.zref_given) blocks = 1;
+    zref_kernel<<<blocks, kZrefThreads, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
+                                                p.zref_given ? 1 : 0, p.z_ref,
+                                                reinterpret_cast<double *>(w + p.off_partials), hdr);
     return cudaGetLastError();
 }
 
@@ -220,46 +243,82 @@ __device__ __forceinline__ void finish_window(int vmin, int vmax, int w, int m, 
     *len = (int)span;
 }
 
-__global__ void __launch_bounds__(1024) bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets,
-                                                        int *__restrict__ cursor, long long n, WsHeader *hdr, int w,
-                                                        int mrx, int mry) {
-    __shared__ int part[1024];
-    const int tid = threadIdx.x;
-    if (tid == 0) {
+// Exclusive prefix sum of the bin counts in two steps: every block scans
+// 1024 bins with warp shuffles and records its total; then every block adds
+// the totals of the blocks before it, seeds the scatter cursors, and the
+// first block finalises the occupied window and the binned sample count.
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    return x - v + (warp > 0 ? warp_tot[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(kScanThreads) bin_scan_local(const int *__restrict__ counts,
+                                                               int *__restrict__ offsets, int *__restrict__ block_sum,
+                                                               long long n) {
+    __shared__ int warp_tot[32];
+    const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
+    const int v = i < n ? counts[i] : 0;
+    const int ex = block_exclusive_scan(v, warp_tot);
+    if (i < n) offsets[i] = ex;
+    if (threadIdx.x == kScanThreads - 1) block_sum[blockIdx.x] = ex + v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) bin_scan_add(int *__restrict__ offsets, int *__restrict__ cursor,
+                                                             const int *__restrict__ block_sum, long long n,
+                                                             int nblocks, WsHeader *hdr, int w, int mrx, int mry) {
+    __shared__ int base_s;
+    if (threadIdx.x < 32) {
+        int acc = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) acc += block_sum[b];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) base_s = acc;
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
+    if (i < n) {
+        const int o = offsets[i] + base_s;
+        offsets[i] = o;
+        cursor[i] = o;
+    }
+    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
+        const int total = base_s + block_sum[blockIdx.x];
+        offsets[n] = total;
+        hdr->n_valid = total;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         finish_window(hdr->u_min, hdr->u_max, w, mrx, &hdr->u_lo, &hdr->u_len);
         finish_window(hdr->v_min, hdr->v_max, w, mry, &hdr->v_lo, &hdr->v_len);
-    }
-    const long long per = (n + 1023) / 1024;
-    const long long b0 = tid * per, b1 = min(n, b0 + per);
-    int s = 0;
-    for (long long b = b0; b < b1; ++b) s += counts[b];
-    part[tid] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over 1024 partial sums
-    for (int d = 1; d < 1024; d <<= 1) {
-        const int v = tid >= d ? part[tid - d] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
-    int run = tid > 0 ? part[tid - 1] : 0;
-    for (long long b = b0; b < b1; ++b) {
-        offsets[b] = run;
-        cursor[b] = run;
-        run += counts[b];
-    }
-    if (tid == 1023) {
-        offsets[n] = part[1023];
-        hdr->n_valid = part[1023];
     }
 }
 
 cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    bin_scan_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts),
-                                       reinterpret_cast<int *>(w + p.off_offsets),
-                                       reinterpret_cast<int *>(w + p.off_cursor), p.n_bins,
-                                       reinterpret_cast<WsHeader *>(w), p.w, p.mrx, p.mry);
+    const int nblocks = (int)((p.n_bins + kScanThreads - 1) / kScanThreads);
+    int *offsets = reinterpret_cast<int *>(w + p.off_offsets);
+    int *bsum = reinterpret_cast<int *>(w + p.off_blocksum);
+    bin_scan_local<<<nblocks, kScanThreads, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts), offsets, bsum,
+                                                   p.n_bins);
+    bin_scan_add<<<nblocks, kScanThreads, 0, s>>>(offsets, reinterpret_cast<int *>(w + p.off_cursor), bsum,
+                                                 p.n_bins, nblocks, reinterpret_cast<WsHeader *>(w), p.w, p.mrx,
+                                                 p.mry);
     return cudaGetLastError();
 }
 

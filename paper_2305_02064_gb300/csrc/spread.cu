@@ -31,45 +31,36 @@ namespace mmsar {
 __global__ void __launch_bounds__(256) spread_weights_kernel(const SampleRec *__restrict__ srec,
                                                              const WsHeader *__restrict__ hdr, int w, float kappa,
                                                              int *__restrict__ dd, float4 *__restrict__ wrec) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    // one thread per record entry: consecutive threads write consecutive
+    // 16-byte entries (entry 0 = header, then w + 3 x quads, w + 3 y quads)
+    const int nq = w + 3, rq = 2 * nq + 1;
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = item / rq;
     if (s >= hdr->n_valid) return;
+    const int e = (int)(item - s * rq);
     const SampleRec r = srec[s];
-    const int nq = w + 3;
-    float4 *out = wrec + (long long)s * (2 * nq + 1);
-    const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
-    dd[s] = d;
-    out[0] = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
-    float wx[18], wy[18];   // taps -3 .. 14 (w <= 12)
+    if (e == 0) {
+        const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
+        dd[s] = d;
+        wrec[item] = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
+        return;
+    }
+    const int q = (e - 1) % nq;                   // quad q = taps q-3 .. q
+    const float f = (e - 1) < nq ? r.fx : r.fy;
+    float v[4];
 #pragma unroll
-    for (int a = 0; a < 18; ++a) {
-        const int tap = a - 3;
-        const float dxa = r.fx - (float)tap, dyb = r.fy - (float)tap;
-        const bool in = tap >= 0 && tap < w;
-        wx[a] = in ? expf(-kappa * dxa * dxa) : 0.f;
-        wy[a] = in ? expf(-kappa * dyb * dyb) : 0.f;
+    for (int i = 0; i < 4; ++i) {
+        const int tap = q - 3 + i;
+        const float d = f - (float)tap;
+        v[i] = (tap >= 0 && tap < w) ? expf(-kappa * d * d) : 0.f;
     }
-    for (int q = 0; q < nq; ++q) {
-        // quad q = taps q-3 .. q = entries q .. q+3 of the padded arrays
-        float4 x, y;
-        switch (q) {   // keep the register arrays statically indexed
-#define MMSAR_Q(Q)                                                              \
-    case Q:                                                                      \
-        x = make_float4(wx[Q], wx[(Q) + 1], wx[(Q) + 2], wx[(Q) + 3]);           \
-        y = make_float4(wy[Q], wy[(Q) + 1], wy[(Q) + 2], wy[(Q) + 3]);           \
-        break;
-            MMSAR_Q(0) MMSAR_Q(1) MMSAR_Q(2) MMSAR_Q(3) MMSAR_Q(4) MMSAR_Q(5) MMSAR_Q(6) MMSAR_Q(7)
-            MMSAR_Q(8) MMSAR_Q(9) MMSAR_Q(10) MMSAR_Q(11) MMSAR_Q(12) MMSAR_Q(13) MMSAR_Q(14)
-#undef MMSAR_Q
-            default: x = y = make_float4(0.f, 0.f, 0.f, 0.f); break;
-        }
-        out[1 + q] = x;
-        out[1 + nq + q] = y;
-    }
+    wrec[item] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 cudaError_t launch_spread_weights(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const unsigned blocks = (unsigned)((p.L + 255) / 256);
+    const long long items = p.L * (2 * (p.w + 3) + 1);
+    const unsigned blocks = (unsigned)((items + 255) / 256);
     spread_weights_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const SampleRec *>(w + p.off_srec),
                                                  reinterpret_cast<const WsHeader *>(w), p.w,
                                                  (float)(1.5 * kPi / p.w), reinterpret_cast<int *>(w + p.off_dd),

@@ -29,9 +29,10 @@ struct StoltArgs {
     float2 *Z;              // [mx][my][nz]
     const WsHeader *hdr;
     int mx, my, nk, nkp, nz, w;
-    double kx_step, ky_step;   // 2 pi / (M d)
-    double k0, dk;             // 2 pi f0 / c, 2 pi df / c
-    double dz, z_c;
+    float kx_step, ky_step;    // 2 pi / (M d)
+    float k0_hi, k0_lo, dk;    // 2 pi f0 / c as a float pair, 2 pi df / c
+    float cells_per_kz;        // dz MRZ / (2 pi)
+    double z_c;                // z0 + (nz / 2) dz
     float kappa;
     float deapod_scale;        // sqrt(pi / tau_z) / MRZ
     float tau_z;
@@ -52,23 +53,24 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
     int *jlo_s = reinterpret_cast<int *>(tbuf + kStoltCols * a.nk);   // [8 * 32]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncol = a.mx * a.my;
+    __shared__ float turns_per_kz_s;   // (z_c - z_ref) / (2 pi): once per CTA (z_ref lives on the device)
+    if (tid == 0) turns_per_kz_s = (float)((a.z_c - a.hdr->z_ref) * (0.5 / kPi));
     const int col = blockIdx.x * kStoltCols + warp;
     for (int e = tid; e < MRZ * GP; e += 256) grid[e] = make_float2(0.f, 0.f);
     fill_twiddles<MRZ, +1>(tw, tid, 256);
     __syncthreads();
     if (col < ncol) {
         const int om = col / a.my, on = col - (col / a.my) * a.my;
-        const float kx = (float)((om - a.mx / 2) * a.kx_step);
-        const float ky = (float)((on - a.my / 2) * a.ky_step);
+        const float kx = (float)(om - a.mx / 2) * a.kx_step;
+        const float ky = (float)(on - a.my / 2) * a.ky_step;
         const float kr2 = kx * kx + ky * ky;
-        const double zoff = a.z_c - a.hdr->z_ref;
-        const float turns_per_kz = (float)(zoff / (2.0 * kPi));
-        const float cells_per_kz = (float)(a.dz * MRZ / (2.0 * kPi));
+        const float turns_per_kz = turns_per_kz_s;
+        const float cells_per_kz = a.cells_per_kz;
         const float2 *Sc = a.S + (long long)col * a.nkp;
         const float hw = 0.5f * a.w;
         // k = 2 pi f / c on the uniform grid, formed as k0_hi + (k0_lo + k dk)
         // (k0 split into two floats): within half an ulp of the FP64 value
-        const float k0_hi = (float)a.k0, k0_lo = (float)(a.k0 - (double)k0_hi), dkf = (float)a.dk;
+        const float k0_hi = a.k0_hi, k0_lo = a.k0_lo, dkf = a.dk;
         auto wavenumber = [&](int k) { return k0_hi + fmaf((float)k, dkf, k0_lo); };
         // k_z grows with k: the evanescent samples (4k^2 <= k_x^2 + k_y^2) form a prefix
         int kf = 0;
@@ -239,11 +241,13 @@ cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
     a.nkp = p.nkp;
     a.nz = p.grid.nz;
     a.w = p.w;
-    a.kx_step = 2.0 * kPi / (p.mx * p.grid.dx);
-    a.ky_step = 2.0 * kPi / (p.my * p.grid.dy);
-    a.k0 = 2.0 * kPi * p.shape.f0_hz / kC0;
-    a.dk = 2.0 * kPi * p.shape.df_hz / kC0;
-    a.dz = p.grid.dz;
+    a.kx_step = (float)(2.0 * kPi / (p.mx * p.grid.dx));
+    a.ky_step = (float)(2.0 * kPi / (p.my * p.grid.dy));
+    const double k0 = 2.0 * kPi * p.shape.f0_hz / kC0;
+    a.k0_hi = (float)k0;
+    a.k0_lo = (float)(k0 - (double)a.k0_hi);
+    a.dk = (float)(2.0 * kPi * p.shape.df_hz / kC0);
+    a.cells_per_kz = (float)(p.grid.dz * p.mrz / (2.0 * kPi));
     a.z_c = p.grid.z0 + (p.grid.nz / 2) * p.grid.dz;
     a.kappa = (float)(1.5 * kPi / p.w);
     a.deapod_scale = (float)(std::sqrt(kPi / p.tau_z) / p.mrz);
