@@ -135,14 +135,12 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
         auto consume = [&](const float4 &x, const float4 &y, const float2 &v) {
             const float wx[4] = {x.x, x.y, x.z, x.w};
             const float wy[4] = {y.x, y.y, y.z, y.w};
+            // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float2 t = make_float2(wy[j] * v.x, wy[j] * v.y);
+                const float2 t = fmul2(make_float2(wy[j], wy[j]), v);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    acc[j][i].x = fmaf(wx[i], t.x, acc[j][i].x);
-                    acc[j][i].y = fmaf(wx[i], t.y, acc[j][i].y);
-                }
+                for (int i = 0; i < 4; ++i) acc[j][i] = ffma2(make_float2(wx[i], wx[i]), t, acc[j][i]);
             }
         };
         if (n > 0) fetch(0, x0, y0, v0);

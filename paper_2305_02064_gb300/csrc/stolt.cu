@@ -123,12 +123,12 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                     const float d0 = t - (float)jl;
                     float wgt = __expf(-a.kappa * d0 * d0);
                     float rho = __expf(a.kappa * (2.f * d0 - 1.f));
+                    // weights and ratios advance together: (w, r) *= (r, q)
+                    float2 wr = make_float2(wgt, rho);
 #pragma unroll
                     for (int i = 0; i < WR; ++i) {
-                        acc[i].x = fmaf(wgt, c.x, acc[i].x);
-                        acc[i].y = fmaf(wgt, c.y, acc[i].y);
-                        wgt *= rho;
-                        rho *= qk;
+                        acc[i] = ffma2(make_float2(wr.x, wr.x), c, acc[i]);
+                        wr = fmul2(wr, make_float2(wr.y, qk));
                     }
                 }
                 float2 *mine = winbuf + (warp * 32 + lane) * WP;
