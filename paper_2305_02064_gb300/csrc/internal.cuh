@@ -33,7 +33,8 @@ struct WsHeader {
     int u_lo, u_len, v_lo, v_len;
     int zref_done;      // blocks of the z_ref reduction that have finished
     int pad_i;
-    double pad[9];
+    double inv_4zc;     // 1 / (4 Z_c), Z_c = z_scene - z_ref (0 without compensation)
+    double pad[8];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 
@@ -62,10 +63,9 @@ struct Plan {
     double z_scene;     // resolved (grid centre when NaN)
     double tau_x, tau_y, tau_z;
     // workspace layout (byte offsets)
-    size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm, off_srec;
+    size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm;
     size_t off_dd, off_wq;   // per sorted sample: in-bin cell offsets; Gaussian weight quads
     size_t off_partials;     // per-block sums of the z_ref reduction
-    size_t off_blocksum;     // per-block totals of the bin scan
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
     // optional per-stage timing events (caller-owned)
@@ -74,7 +74,7 @@ struct Plan {
 };
 
 constexpr int kStages = 8;
-constexpr int kKernelsPerImage = 14;
+constexpr int kKernelsPerImage = 12;
 
 }  // namespace mmsar
 
@@ -92,9 +92,8 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
                             cudaStream_t s);
 cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
-cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
-cudaError_t launch_spread_weights(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_sort_and_weigh(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);

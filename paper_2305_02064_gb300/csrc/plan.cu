@@ -148,7 +148,6 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     };
     const size_t L = (size_t)p.L;
     p.off_partials = take(sizeof(double) * 128);
-    p.off_blocksum = take(sizeof(int) * (size_t)((p.n_bins + 1023) / 1024));
     p.off_counts = take(sizeof(int) * (size_t)p.n_bins);
     p.off_offsets = take(sizeof(int) * ((size_t)p.n_bins + 1));
     p.off_cursor = take(sizeof(int) * (size_t)p.n_bins);
@@ -156,7 +155,6 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_rec = take(sizeof(SampleRec) * L);
     p.off_phase = take(sizeof(uint2) * L);
     p.off_perm = take(sizeof(int) * L);
-    p.off_srec = take(sizeof(SampleRec) * L);
     p.off_dd = take(sizeof(int) * L);
     p.off_wq = take(sizeof(float4) * (size_t)(2 * p.w + 7) * L);
     p.off_shat = take(sizeof(float2) * (size_t)p.n_kc * L * kKC);
@@ -282,8 +280,7 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_STEP(launch_geometry(p, workspace, pos, tx, rx, s), "geometry");
     MMSAR_STEP(launch_bin_scan(p, workspace, s), "bin scan");
     MMSAR_STEP(launch_bin_scatter(p, workspace, s), "bin scatter");
-    MMSAR_STEP(launch_bin_sort(p, workspace, s), "bin sort");
-    MMSAR_STEP(launch_spread_weights(p, workspace, s), "gridding weights");
+    MMSAR_STEP(launch_sort_and_weigh(p, workspace, s), "bin sort and gridding weights");
     MMSAR_MARK(1);
     MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation");
     MMSAR_MARK(2);

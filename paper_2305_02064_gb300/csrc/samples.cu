@@ -6,7 +6,9 @@
 //                   d^z = z_l - z_ref; the residual beta of Eq. 12; the
 //                   gridding position on the 2M-point oversampled aperture
 //                   grid; the compensation phase as 32-bit fixed-point turns.
-//  bin_*            counting sort of the samples by 4x4-cell bin.
+//  bin_*            counting sort of the samples by 4x4-cell bin (the
+//                   in-bin ordering is finished with the gridding weights,
+//                   in spread.cu).
 //  compensate       Eq. 11, s_hat = s exp(+j k beta), written in bin order.
 //
 // Precision: FP64 is used once per sample (geometry and the phase argument
@@ -27,22 +29,32 @@ namespace mmsar {
 // Mean of z_l = p_z + (tx_z + rx_z)/2 over all samples, i.e.
 // mean(p_z) + (mean(tx_z) + mean(rx_z))/2.  Every block sums a fixed slice of
 // the positions in a fixed order and the last block to finish adds the block
-// sums in index order, so the result is the same bits on every run.  Block 0
-// also resets the occupied-window accumulators of the header.
+// sums in index order, so the result is the same bits on every run.  The
+// finishing thread also resolves Z_c = z_scene - z_ref of Eq. 12 once for
+// all samples (its reciprocal term 1 / (4 Z_c), and the check Z_c > 0).
+// Block 0 resets the occupied-window accumulators of the header.
 constexpr int kZrefThreads = 256;
 constexpr int kZrefMaxBlocks = 128;
+
+__device__ __forceinline__ void resolve_zref(double z_ref, double z_scene, int compensate, WsHeader *hdr) {
+    hdr->z_ref = z_ref;
+    const double Zc = z_scene - z_ref;
+    if (compensate && !(Zc > 0.0)) atomicOr(&hdr->error, kErrGeometry);
+    hdr->inv_4zc = (compensate && Zc > 0.0) ? 1.0 / (4.0 * Zc) : 0.0;
+}
 
 __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__restrict__ pos, int P,
                                                             const double *__restrict__ tx, int T,
                                                             const double *__restrict__ rx, int R, int given,
-                                                            double z_given, double *partials, WsHeader *hdr) {
+                                                            double z_given, double z_scene, int compensate,
+                                                            double *partials, WsHeader *hdr) {
     __shared__ double red[kZrefThreads];
     __shared__ bool last;
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) {
         hdr->u_min = hdr->v_min = 0x7fffffff;
         hdr->u_max = hdr->v_max = -0x7fffffff - 1;
-        if (given) hdr->z_ref = z_given;
+        if (given) resolve_zref(z_given, z_scene, compensate, hdr);
     }
     if (given) return;
     const int per = (P + gridDim.x - 1) / gridDim.x;
@@ -68,7 +80,7 @@ __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__rest
         double st = 0.0, sr = 0.0;
         for (int t = 0; t < T; ++t) st += tx[3 * t + 2];
         for (int r = 0; r < R; ++r) sr += rx[3 * r + 2];
-        hdr->z_ref = (P > 0 ? sum / P : 0.0) + 0.5 * (st / T + sr / R);
+        resolve_zref((P > 0 ? sum / P : 0.0) + 0.5 * (st / T + sr / R), z_scene, compensate, hdr);
     }
 }
 
@@ -76,11 +88,12 @@ cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double
                         cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
-    int blocks = (p.shape.n_pos + 2047) / 2048;
+    // about one position per thread, at most kZrefMaxBlocks blocks
+    int blocks = (p.shape.n_pos + kZrefThreads - 1) / kZrefThreads;
     blocks = blocks < 1 ? 1 : (blocks > kZrefMaxBlocks ? kZrefMaxBlocks : blocks);
     if (p.zref_given) blocks = 1;
     zref_kernel<<<blocks, kZrefThreads, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
-                                                p.zref_given ? 1 : 0, p.z_ref,
+                                                p.zref_given ? 1 : 0, p.z_ref, p.z_scene, p.opt.compensate,
                                                 reinterpret_cast<double *>(w + p.off_partials), hdr);
     return cudaGetLastError();
 }
@@ -89,9 +102,8 @@ cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double
 struct GeomArgs {
     const double *pos, *tx, *rx;
     int T, R, P;
-    long long L;
+    int L;                               // below 2^30 (plan limit)
     double x_c, y_c, inv_dx2, inv_dy2;   // 2 / dx: cells of the 2M grid per metre
-    double z_scene;
     int compensate;
     double half_w;
     int mrx, mry, nbx;
@@ -123,10 +135,9 @@ __device__ __forceinline__ void box_reduce(int umin, int umax, int vmin, int vma
     }
 }
 
-__device__ void geometry_one(const GeomArgs &a, long long l, int &umin, int &umax, int &vmin, int &vmax) {
-    const int p = (int)(l % a.P);
-    const int r = (int)((l / a.P) % a.R);
-    const int t = (int)(l / ((long long)a.P * a.R));
+__device__ void geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int &vmin, int &vmax) {
+    const int tr = l / a.P, p = l - tr * a.P;
+    const int t = tr / a.R, r = tr - t * a.R;
     const double px = a.pos[3 * p], py = a.pos[3 * p + 1], pz = a.pos[3 * p + 2];
     // Tx / Rx absolute positions (Eq. 2 geometry)
     const double xT = px + a.tx[3 * t], yT = py + a.tx[3 * t + 1], zT = pz + a.tx[3 * t + 2];
@@ -134,22 +145,15 @@ __device__ void geometry_one(const GeomArgs &a, long long l, int &umin, int &uma
     // Eq. 3-4: virtual element at the midpoint, separations, plane offset
     const double xv = 0.5 * (xT + xR), yv = 0.5 * (yT + yR), zl = 0.5 * (zT + zR);
     const double ddx = xR - xT, ddy = yR - yT;
-    const double z_ref = a.hdr->z_ref;
-    const double Zc = a.z_scene - z_ref;
+    const double z_ref = a.hdr->z_ref, inv_4zc = a.hdr->inv_4zc;
     if (!(isfinite(xv) && isfinite(yv) && isfinite(zl))) {
         atomicOr(&a.hdr->error, kErrNonfinite);
         a.binid[l] = -1;
         return;
     }
-    double beta = 0.0;
-    if (a.compensate) {
-        if (!(Zc > 0.0)) {
-            atomicOr(&a.hdr->error, kErrGeometry);
-        } else {
-            // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
-            beta = -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) / (4.0 * Zc);
-        }
-    }
+    // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
+    // (Z_c <= 0 was flagged once when z_ref was resolved; beta is then 0)
+    const double beta = (a.compensate && inv_4zc > 0.0) ? -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) * inv_4zc : 0.0;
     // position on the 2M-point periodic grid, in cells
     const double gx = (xv - a.x_c) * a.inv_dx2;
     const double gy = (yv - a.y_c) * a.inv_dy2;
@@ -162,12 +166,14 @@ __device__ void geometry_one(const GeomArgs &a, long long l, int &umin, int &uma
     umax = ufar ? 1073741823 : (int)u0d;
     vmin = vfar ? -1073741824 : (int)v0d;
     vmax = vfar ? 1073741823 : (int)v0d;
-    long long u0 = (long long)u0d % a.mrx, v0 = (long long)v0d % a.mry;
-    if (u0 < 0) u0 += a.mrx;
-    if (v0 < 0) v0 += a.mry;
+    // wrap into [0, M_r) (M_r is a power of two; beyond 2^62 cells the
+    // position is meaningless and is put at cell 0)
+    const long long u0l = fabs(u0d) < 4.0e18 ? (long long)u0d : 0;
+    const long long v0l = fabs(v0d) < 4.0e18 ? (long long)v0d : 0;
+    const int u0 = (int)(u0l & (a.mrx - 1)), v0 = (int)(v0l & (a.mry - 1));
     SampleRec rc;
-    rc.u0 = (int)u0;
-    rc.v0 = (int)v0;
+    rc.u0 = u0;
+    rc.v0 = v0;
     rc.fx = (float)fx;
     rc.fy = (float)fy;
     a.rec[l] = rc;
@@ -179,7 +185,7 @@ __device__ void geometry_one(const GeomArgs &a, long long l, int &umin, int &uma
 }
 
 __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     int bumin = 0x7fffffff, bumax = -0x7fffffff - 1, bvmin = 0x7fffffff, bvmax = -0x7fffffff - 1;
     if (l < a.L) {
         geometry_one(a, l, bumin, bumax, bvmin, bvmax);
@@ -197,12 +203,11 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
     a.T = p.shape.n_tx;
     a.R = p.shape.n_rx;
     a.P = p.shape.n_pos;
-    a.L = p.L;
+    a.L = (int)p.L;
     a.x_c = p.grid.x0 + (p.grid.nx / 2) * p.grid.dx;
     a.y_c = p.grid.y0 + (p.grid.ny / 2) * p.grid.dy;
     a.inv_dx2 = (double)p.mrx / ((double)p.mx * p.grid.dx);
     a.inv_dy2 = (double)p.mry / ((double)p.my * p.grid.dy);
-    a.z_scene = p.z_scene;
     a.compensate = p.opt.compensate;
     a.half_w = 0.5 * p.w;
     a.mrx = p.mrx;
@@ -221,8 +226,6 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
 }
 
 // ------------------------------------------------------------------ bin scan
-// Exclusive prefix sum of the bin counts (one block); also seeds the scatter
-// cursors and records the number of binned samples.
 // Occupied window of one axis from the min / max first cell: cells
 // lo .. lo + len - 1 (mod m) can receive a tap.
 __device__ __forceinline__ void finish_window(int vmin, int vmax, int w, int m, int *lo, int *len) {
@@ -243,11 +246,14 @@ __device__ __forceinline__ void finish_window(int vmin, int vmax, int w, int m, 
     *len = (int)span;
 }
 
-// Exclusive prefix sum of the bin counts in two steps: every block scans
-// 1024 bins with warp shuffles and records its total; then every block adds
-// the totals of the blocks before it, seeds the scatter cursors, and the
-// first block finalises the occupied window and the binned sample count.
+// Exclusive prefix sum of the bin counts in one block, in rounds of
+// kScanThreads x kScanPer bins: thread t loads its kScanPer consecutive bins
+// with 16-byte loads, the block scans the per-thread sums with warp shuffles,
+// and every thread writes its bins' offsets (also the scatter cursors); the
+// running total carries to the next round.  The bin count is a multiple of 4.
+// Thread 0 finalises the occupied window and the binned-sample count.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 16;
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -270,40 +276,39 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
     return x - v + (warp > 0 ? warp_tot[warp - 1] : 0);
 }
 
-__global__ void __launch_bounds__(kScanThreads) bin_scan_local(const int *__restrict__ counts,
-                                                               int *__restrict__ offsets, int *__restrict__ block_sum,
-                                                               long long n) {
+__global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const int *__restrict__ counts,
+                                                                int *__restrict__ offsets, int *__restrict__ cursor,
+                                                                int n, WsHeader *hdr, int w, int mrx, int mry) {
     __shared__ int warp_tot[32];
-    const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
-    const int v = i < n ? counts[i] : 0;
-    const int ex = block_exclusive_scan(v, warp_tot);
-    if (i < n) offsets[i] = ex;
-    if (threadIdx.x == kScanThreads - 1) block_sum[blockIdx.x] = ex + v;
-}
-
-__global__ void __launch_bounds__(kScanThreads) bin_scan_add(int *__restrict__ offsets, int *__restrict__ cursor,
-                                                             const int *__restrict__ block_sum, long long n,
-                                                             int nblocks, WsHeader *hdr, int w, int mrx, int mry) {
-    __shared__ int base_s;
-    if (threadIdx.x < 32) {
-        int acc = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) acc += block_sum[b];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) base_s = acc;
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanThreads * kScanPer) {
+        const int b0 = base + threadIdx.x * kScanPer;
+        int4 c[kScanPer / 4];
+        int sum = 0;
+#pragma unroll
+        for (int q = 0; q < kScanPer / 4; ++q) {
+            c[q] = b0 + 4 * q < n ? *reinterpret_cast<const int4 *>(counts + b0 + 4 * q) : make_int4(0, 0, 0, 0);
+            sum += c[q].x + c[q].y + c[q].z + c[q].w;
+        }
+        int run = carry + block_exclusive_scan(sum, warp_tot);
+#pragma unroll
+        for (int q = 0; q < kScanPer / 4; ++q) {
+            if (b0 + 4 * q >= n) break;
+            int4 o;
+            o.x = run;
+            o.y = o.x + c[q].x;
+            o.z = o.y + c[q].y;
+            o.w = o.z + c[q].z;
+            run = o.w + c[q].w;
+            *reinterpret_cast<int4 *>(offsets + b0 + 4 * q) = o;
+            *reinterpret_cast<int4 *>(cursor + b0 + 4 * q) = o;
+        }
+        carry += warp_tot[31];
+        __syncthreads();   // warp_tot is reused by the next round
     }
-    __syncthreads();
-    const long long i = (long long)blockIdx.x * kScanThreads + threadIdx.x;
-    if (i < n) {
-        const int o = offsets[i] + base_s;
-        offsets[i] = o;
-        cursor[i] = o;
-    }
-    if (blockIdx.x == nblocks - 1 && threadIdx.x == 0) {
-        const int total = base_s + block_sum[blockIdx.x];
-        offsets[n] = total;
-        hdr->n_valid = total;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+        offsets[n] = carry;
+        hdr->n_valid = carry;
         finish_window(hdr->u_min, hdr->u_max, w, mrx, &hdr->u_lo, &hdr->u_len);
         finish_window(hdr->v_min, hdr->v_max, w, mry, &hdr->v_lo, &hdr->v_len);
     }
@@ -311,90 +316,31 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_add(int *__restrict__ o
 
 cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const int nblocks = (int)((p.n_bins + kScanThreads - 1) / kScanThreads);
-    int *offsets = reinterpret_cast<int *>(w + p.off_offsets);
-    int *bsum = reinterpret_cast<int *>(w + p.off_blocksum);
-    bin_scan_local<<<nblocks, kScanThreads, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts), offsets, bsum,
-                                                   p.n_bins);
-    bin_scan_add<<<nblocks, kScanThreads, 0, s>>>(offsets, reinterpret_cast<int *>(w + p.off_cursor), bsum,
-                                                 p.n_bins, nblocks, reinterpret_cast<WsHeader *>(w), p.w, p.mrx,
-                                                 p.mry);
+    bin_scan_kernel<<<1, kScanThreads, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts),
+                                               reinterpret_cast<int *>(w + p.off_offsets),
+                                               reinterpret_cast<int *>(w + p.off_cursor), (int)p.n_bins,
+                                               reinterpret_cast<WsHeader *>(w), p.w, p.mrx, p.mry);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ bin scatter
-__global__ void __launch_bounds__(256) bin_scatter_kernel(long long L, const int *__restrict__ binid,
-                                                          const SampleRec *__restrict__ rec,
-                                                          int *__restrict__ cursor, int *__restrict__ perm,
-                                                          SampleRec *__restrict__ srec) {
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Each sample takes the next slot of its bin (arrival order of the atomics;
+// the in-bin order is made deterministic afterwards, see spread.cu).
+__global__ void __launch_bounds__(256) bin_scatter_kernel(int L, const int *__restrict__ binid,
+                                                          int *__restrict__ cursor, int *__restrict__ perm) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= L) return;
     const int b = binid[l];
     if (b < 0) return;
-    const int slot = atomicAdd(&cursor[b], 1);
-    perm[slot] = (int)l;
-    srec[slot] = rec[l];
+    perm[atomicAdd(&cursor[b], 1)] = l;
 }
 
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
     const unsigned blocks = (unsigned)((p.L + 255) / 256);
-    bin_scatter_kernel<<<blocks, 256, 0, s>>>(p.L, reinterpret_cast<int *>(w + p.off_binid),
-                                              reinterpret_cast<SampleRec *>(w + p.off_rec),
+    bin_scatter_kernel<<<blocks, 256, 0, s>>>((int)p.L, reinterpret_cast<int *>(w + p.off_binid),
                                               reinterpret_cast<int *>(w + p.off_cursor),
-                                              reinterpret_cast<int *>(w + p.off_perm),
-                                              reinterpret_cast<SampleRec *>(w + p.off_srec));
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ bin sort
-// The scatter above fills each bin in the arrival order of its atomics.  To
-// make the image bit-reproducible, every bin of up to 256 samples is put in
-// ascending sample order by a rank sort (one warp per bin); bins are small
-// (a few to a few hundred samples at the paper's sampling densities).
-__global__ void __launch_bounds__(256) bin_sort_kernel(long long n_bins, const int *__restrict__ offsets,
-                                                       int *__restrict__ perm, SampleRec *__restrict__ srec,
-                                                       const SampleRec *__restrict__ rec) {
-    const long long b = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (b >= n_bins) return;
-    const int lane = threadIdx.x & 31;
-    const int beg = offsets[b], n = offsets[b + 1] - beg;
-    if (n <= 1) return;
-    int *pp = perm + beg;
-    // rank sort: element i goes to position #{j : key_j < key_i} (keys are distinct)
-    // done in two sweeps through a small per-warp staging area in shared memory
-    __shared__ int keys[8][256];
-    if (n <= 256) {
-        for (int i = lane; i < n; i += 32) keys[threadIdx.x / 32][i] = pp[i];
-        __syncwarp();
-        int dst[8];
-        int cnt = 0;
-        for (int i = lane; i < n; i += 32) {
-            const int ki = keys[threadIdx.x / 32][i];
-            int rank = 0;
-            for (int j = 0; j < n; ++j) rank += keys[threadIdx.x / 32][j] < ki;
-            dst[cnt++] = rank;
-        }
-        __syncwarp();
-        cnt = 0;
-        for (int i = lane; i < n; i += 32) {
-            const int ki = keys[threadIdx.x / 32][i];
-            const int r = dst[cnt++];
-            pp[r] = ki;
-            srec[beg + r] = rec[ki];
-        }
-    }
-    // larger bins keep arrival order (still correct; only the summation
-    // order, hence the last bits, can then vary between runs)
-}
-
-cudaError_t launch_bin_sort(const Plan &p, void *ws, cudaStream_t s) {
-    char *w = reinterpret_cast<char *>(ws);
-    const unsigned blocks = (unsigned)((p.n_bins + 7) / 8);
-    bin_sort_kernel<<<blocks, 256, 0, s>>>(p.n_bins, reinterpret_cast<int *>(w + p.off_offsets),
-                                           reinterpret_cast<int *>(w + p.off_perm),
-                                           reinterpret_cast<SampleRec *>(w + p.off_srec),
-                                           reinterpret_cast<SampleRec *>(w + p.off_rec));
+                                              reinterpret_cast<int *>(w + p.off_perm));
     return cudaGetLastError();
 }
 

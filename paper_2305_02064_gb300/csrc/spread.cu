@@ -7,64 +7,104 @@
 // cell size h = 2 pi / (2M); the sample reaches the w cells
 // u0 .. u0 + w - 1, u0 = ceil(g - w/2) (indices modulo the grid size).
 //
-// spread_weights_kernel (once per sample, bin order): the sample's offset
-// inside its 4x4-cell bin and, per axis, w + 3 "quads" -- quad q holds the
-// weights of taps q-3 .. q (zero outside 0..w-1), i.e. exactly the four
-// weights a 4-cell block needs when it starts q - 3 cells after u0.
+// sort_and_weigh_kernel (one warp per bin): puts the samples of the bin in
+// ascending sample order (the scatter filled it in the arrival order of its
+// atomics; a fixed order makes the image bit-reproducible) and writes, per
+// sample in that order, its offset inside the 4x4-cell bin and, per axis,
+// w + 3 "quads" -- quad q holds the weights of taps q-3 .. q (zero outside
+// 0..w-1), i.e. exactly the four weights a 4-cell block needs when it starts
+// q - 3 cells after u0.
 //
-// spread_kernel: a CTA owns a 16x8 tile of grid cells and one chunk of 32
-// frequencies; each of its 8 warps owns a 4x4 block of cells and keeps the
-// 16 complex accumulators of its lane's frequency in registers.  Warps work
-// independently (no block barrier): a warp walks the bins whose samples can
-// reach its block, tests 32 samples at a time (one lane each) for overlap with
-// the block and appends the overlapping ones to a list in shared memory, then
-// applies the list with the loads of the entry two ahead already in flight.  For a bin d
-// bins before the block, the block starts 4 d - (in-bin offset) cells after
-// the sample's first tap, which selects one weight quad per axis (two 16-byte
-// broadcast loads).  No two warps write the same cell: no atomics, a fixed
-// summation order.
+// spread_kernel: a CTA owns a 16x8 tile of grid cells and two chunks of 32
+// frequencies; each of its 8 warps owns a 4x4 block of cells, and each lane
+// keeps in registers the 16 complex accumulators of its frequency in both
+// chunks (the per-sample list entry, weight loads and loop control are shared
+// by the two).  Warps work independently (no block barrier): a warp walks the
+// bins whose samples can reach its block, tests 32 samples at a time (one lane
+// each) for overlap with the block and appends the overlapping ones to a list
+// in shared memory, then applies the list with the loads of the next three
+// entries in flight.  For a bin d bins before the block, the block starts
+// 4 d - (in-bin offset) cells after the sample's first tap, which selects one
+// weight quad per axis (two 16-byte broadcast loads).  No two warps write the
+// same cell: no atomics, a fixed summation order.
 #include "fft.cuh"
 #include "internal.cuh"
 
 namespace mmsar {
 
-__global__ void __launch_bounds__(256) spread_weights_kernel(const SampleRec *__restrict__ srec,
-                                                             const WsHeader *__restrict__ hdr, int w, float kappa,
-                                                             int *__restrict__ dd, float4 *__restrict__ wrec) {
-    // one thread per record entry: consecutive threads write consecutive
-    // 16-byte entries (entry 0 = header, then w + 3 x quads, w + 3 y quads)
+constexpr int kSortBinCap = 256;   // bins up to this size are sorted in shared memory
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(kSortWarps * 32) sort_and_weigh_kernel(int n_bins, const int *__restrict__ offsets,
+                                                                       int *__restrict__ perm,
+                                                                       const SampleRec *__restrict__ rec, int w,
+                                                                       float kappa, int *__restrict__ dd,
+                                                                       float4 *__restrict__ wrec) {
+    __shared__ int keys[kSortWarps][kSortBinCap];
+    __shared__ int sorted[kSortWarps][kSortBinCap];
+    __shared__ SampleRec recs[kSortWarps][kSortBinCap];
+    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * kSortWarps + wb;
+    if (b >= n_bins) return;
+    const int beg = offsets[b], n = offsets[b + 1] - beg;
+    if (n == 0) return;
+    int *pp = perm + beg;
+    // rank sort: sample i goes to #{j : key_j < key_i} (sample indices are
+    // distinct); larger bins keep the arrival order (still correct, only the
+    // last bits of the image can then vary between runs)
+    const bool small = n <= kSortBinCap;
+    if (small) {
+        for (int i = lane; i < n; i += 32) keys[wb][i] = pp[i];
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int ki = keys[wb][i];
+            int rank = 0;
+            for (int j = 0; j < n; ++j) rank += keys[wb][j] < ki;
+            sorted[wb][rank] = ki;
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int l = sorted[wb][i];
+            pp[i] = l;
+            recs[wb][i] = rec[l];
+        }
+        __syncwarp();
+    }
+    // weight records of the bin's samples: consecutive lanes write consecutive
+    // 16-byte entries (per sample: a header, w + 3 x quads, w + 3 y quads)
     const int nq = w + 3, rq = 2 * nq + 1;
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long s = item / rq;
-    if (s >= hdr->n_valid) return;
-    const int e = (int)(item - s * rq);
-    const SampleRec r = srec[s];
-    if (e == 0) {
-        const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
-        dd[s] = d;
-        wrec[item] = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
-        return;
-    }
-    const int q = (e - 1) % nq;                   // quad q = taps q-3 .. q
-    const float f = (e - 1) < nq ? r.fx : r.fy;
-    float v[4];
+    const int total = n * rq;
+    for (int e = lane; e < total; e += 32) {
+        const int sl = e / rq, ent = e - sl * rq;
+        const SampleRec r = small ? recs[wb][sl] : rec[pp[sl]];
+        float4 out;
+        if (ent == 0) {
+            const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
+            dd[beg + sl] = d;
+            out = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
+        } else {
+            const int q = (ent - 1) % nq;                 // quad q = taps q-3 .. q
+            const float f = (ent - 1) < nq ? r.fx : r.fy;
+            float v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int tap = q - 3 + i;
-        const float d = f - (float)tap;
-        v[i] = (tap >= 0 && tap < w) ? expf(-kappa * d * d) : 0.f;
+            for (int i = 0; i < 4; ++i) {
+                const int tap = q - 3 + i;
+                const float dlt = f - (float)tap;
+                v[i] = (tap >= 0 && tap < w) ? expf(-kappa * dlt * dlt) : 0.f;
+            }
+            out = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        wrec[(long long)(beg + sl) * rq + ent] = out;
     }
-    wrec[item] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-cudaError_t launch_spread_weights(const Plan &p, void *ws, cudaStream_t s) {
+cudaError_t launch_sort_and_weigh(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const long long items = p.L * (2 * (p.w + 3) + 1);
-    const unsigned blocks = (unsigned)((items + 255) / 256);
-    spread_weights_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const SampleRec *>(w + p.off_srec),
-                                                 reinterpret_cast<const WsHeader *>(w), p.w,
-                                                 (float)(1.5 * kPi / p.w), reinterpret_cast<int *>(w + p.off_dd),
-                                                 reinterpret_cast<float4 *>(w + p.off_wq));
+    const unsigned blocks = (unsigned)((p.n_bins + kSortWarps - 1) / kSortWarps);
+    sort_and_weigh_kernel<<<blocks, kSortWarps * 32, 0, s>>>(
+        (int)p.n_bins, reinterpret_cast<const int *>(w + p.off_offsets), reinterpret_cast<int *>(w + p.off_perm),
+        reinterpret_cast<const SampleRec *>(w + p.off_rec), p.w, (float)(1.5 * kPi / p.w),
+        reinterpret_cast<int *>(w + p.off_dd), reinterpret_cast<float4 *>(w + p.off_wq));
     return cudaGetLastError();
 }
 
@@ -93,17 +133,21 @@ __device__ __forceinline__ bool tile_meets(int t0, int span, int lo, int len, in
 
 constexpr int kSpreadThreads = 256;   // 8 warps: a 16 x 8-cell tile
 
-constexpr int kListCap = 192;   // relevant samples listed per warp before they are applied
+constexpr int kListCap = 192;
+constexpr int kSpreadChunks = 2;   // frequency chunks of 32 per CTA   // relevant samples listed per warp before they are applied
 
-__global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a) {
+template <int NF, int NS, int MINB>
+__global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs a) {
     // per warp: (x-quad index, y-quad index, sample index) of each listed sample
     __shared__ int4 lists[kSpreadThreads / 32][kListCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx >> 4;
-    // the frequency chunk varies fastest, so the chunks of one tile run
-    // together and share the tile's weight records in L2
-    const int kc = blockIdx.x % a.n_kc;
-    const int tile = blockIdx.x / a.n_kc;
+    // a CTA covers NF frequency chunks (a lane holds NF frequencies); the
+    // chunk group varies fastest, so the groups of one tile run together and
+    // share the tile's weight records in L2
+    const int n_kg = (a.n_kc + NF - 1) / NF;
+    const int kg = blockIdx.x % n_kg;
+    const int tile = blockIdx.x / n_kg;
     // tiles outside the occupied window stay unwritten: the FFT along x'
     // reads only the window and takes the rest as zero
     if (!tile_meets((tile % tiles_x) * 16, 16, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
@@ -113,48 +157,63 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
     const int V = (tile / tiles_x) * 8 + (warp >> 2) * 4;
     const int rq = 2 * (a.w + 3) + 1;
     const int nq = a.w + 3;
-    float2 acc[4][4];
+    // chunks past the last one (odd chunk count) repeat it and are not stored
+    int kc[NF];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int f = 0; f < NF; ++f) kc[f] = min(kg * NF + f, a.n_kc - 1);
+    float2 acc[NF][4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = make_float2(0.f, 0.f);
-    const float2 *sh = a.shat + (long long)kc * a.Lmax * kKC + lane;
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[f][j][i] = make_float2(0.f, 0.f);
+    const float2 *sh = a.shat + (long long)kc[0] * a.Lmax * kKC + lane;
+    const long long kstride = NF > 1 ? (long long)(kc[NF - 1] - kc[0]) * a.Lmax * kKC : 0;
     int4 *list = lists[warp];
 
-    // apply the listed samples through a three-deep pipeline: the loads of
-    // entry i + 3 are issued as soon as entry i has been accumulated
+    // one listed sample in flight: its x and y weight quads and its values
+    struct Stage {
+        float4 x, y;
+        float2 v[NF];
+    };
+    // apply the listed samples through an NS-deep pipeline: the loads of
+    // entry i + NS are issued as soon as entry i has been accumulated
     auto apply = [&](int n) {
-        float4 x0, y0, x1, y1, x2, y2;
-        float2 v0, v1, v2;
-        auto fetch = [&](int i, float4 &x, float4 &y, float2 &v) {
+        Stage st[NS];
+        auto fetch = [&](int i, Stage &q) {
             const int4 e = list[i];
-            x = __ldg(a.wrec + e.x);
-            y = __ldg(a.wrec + e.y);
-            v = __ldg(sh + (e.z << 5));
+            q.x = __ldg(a.wrec + e.x);
+            q.y = __ldg(a.wrec + e.y);
+            const float2 *p = sh + (e.z << 5);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q.v[f] = __ldg(p + f * kstride);
         };
-        auto consume = [&](const float4 &x, const float4 &y, const float2 &v) {
-            const float wx[4] = {x.x, x.y, x.z, x.w};
-            const float wy[4] = {y.x, y.y, y.z, y.w};
+        auto consume = [&](const Stage &q) {
+            const float wx[4] = {q.x.x, q.x.y, q.x.z, q.x.w};
+            const float wy[4] = {q.y.x, q.y.y, q.y.z, q.y.w};
             // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float2 t = fmul2(make_float2(wy[j], wy[j]), v);
+                const float2 wyj = make_float2(wy[j], wy[j]);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[j][i] = ffma2(make_float2(wx[i], wx[i]), t, acc[j][i]);
+                for (int f = 0; f < NF; ++f) {
+                    const float2 t = fmul2(wyj, q.v[f]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[f][j][i] = ffma2(make_float2(wx[i], wx[i]), t, acc[f][j][i]);
+                }
             }
         };
-        if (n > 0) fetch(0, x0, y0, v0);
-        if (n > 1) fetch(1, x1, y1, v1);
-        if (n > 2) fetch(2, x2, y2, v2);
-        for (int i = 0; i < n; i += 3) {
-            consume(x0, y0, v0);
-            if (i + 3 < n) fetch(i + 3, x0, y0, v0);
-            if (i + 1 >= n) break;
-            consume(x1, y1, v1);
-            if (i + 4 < n) fetch(i + 4, x1, y1, v1);
-            if (i + 2 >= n) break;
-            consume(x2, y2, v2);
-            if (i + 5 < n) fetch(i + 5, x2, y2, v2);
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if (k < n) fetch(k, st[k]);
+        for (int i = 0; i < n; i += NS) {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                if (i + k >= n) break;
+                consume(st[k]);
+                if (i + k + NS < n) fetch(i + k + NS, st[k]);
+            }
         }
     };
 
@@ -196,11 +255,15 @@ __global__ void __launch_bounds__(kSpreadThreads, 3) spread_kernel(SpreadArgs a)
     }
     __syncwarp();
     apply(n);
-    float2 *g = a.G + (long long)kc * a.mry * a.mrx * kKC;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int f = 0; f < NF; ++f) {
+        if (f > 0 && kg * NF + f >= a.n_kc) break;
+        float2 *g = a.G + (long long)kc[f] * a.mry * a.mrx * kKC;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC + lane] = acc[j][i];
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC + lane] = acc[f][j][i];
+    }
 }
 
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
@@ -220,8 +283,10 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
-    const unsigned blocks = (unsigned)((p.mrx / 16) * (p.mry / 8) * p.n_kc);
-    spread_kernel<<<blocks, kSpreadThreads, 0, s>>>(a);
+    // two frequency chunks per CTA (a lane holds two frequencies), three
+    // listed samples in flight, two CTAs per SM
+    const unsigned tiles = (unsigned)((p.mrx / 16) * (p.mry / 8));
+    spread_kernel<kSpreadChunks, 3, 2><<<tiles * ((p.n_kc + kSpreadChunks - 1) / kSpreadChunks), kSpreadThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
