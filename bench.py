@@ -237,8 +237,10 @@ def stage_bytes(plan, scan):
     Z = mx * my * nz * c
     B = mx * ny * nz * c
     V = nx * ny * nz * c
-    rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 4
-    return {"prep": L * (60 + rec) + 24 * P, "compensate": echo + shat + L * 12, "grid": shat + G + L * rec,
+    rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 8   # weight record + (in-bin offset, sample index)
+    # prep: geometry records, phases, bin ids, permutation; compensate: echo
+    # in, s_hat out, phases, and (same launch) the in-bin sort and records
+    return {"prep": L * 36 + 24 * P, "compensate": echo + shat + L * 8 + L * (24 + rec), "grid": shat + G + L * rec,
             "fft_x": G + A, "fft_y": A + S, "stolt": S + Z, "ifft_y": Z + B, "ifft_x": B + V}
 
 

@@ -64,7 +64,7 @@ struct Plan {
     double tau_x, tau_y, tau_z;
     // workspace layout (byte offsets)
     size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm;
-    size_t off_dd, off_wq;   // per sorted sample: in-bin cell offsets; Gaussian weight quads
+    size_t off_dd, off_wq;   // per sorted sample: (in-bin cell offset, sample index); Gaussian weight quads
     size_t off_partials;     // per-block sums of the z_ref reduction
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
@@ -74,7 +74,7 @@ struct Plan {
 };
 
 constexpr int kStages = 8;
-constexpr int kKernelsPerImage = 12;
+constexpr int kKernelsPerImage = 11;
 
 }  // namespace mmsar
 
@@ -93,7 +93,6 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
 cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
-cudaError_t launch_sort_and_weigh(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);

@@ -155,7 +155,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_rec = take(sizeof(SampleRec) * L);
     p.off_phase = take(sizeof(uint2) * L);
     p.off_perm = take(sizeof(int) * L);
-    p.off_dd = take(sizeof(int) * L);
+    p.off_dd = take(sizeof(int2) * L);
     p.off_wq = take(sizeof(float4) * (size_t)(2 * p.w + 7) * L);
     p.off_shat = take(sizeof(float2) * (size_t)p.n_kc * L * kKC);
     const size_t G = sizeof(float2) * (size_t)p.n_kc * p.mry * p.mrx * kKC;
@@ -280,9 +280,8 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_STEP(launch_geometry(p, workspace, pos, tx, rx, s), "geometry");
     MMSAR_STEP(launch_bin_scan(p, workspace, s), "bin scan");
     MMSAR_STEP(launch_bin_scatter(p, workspace, s), "bin scatter");
-    MMSAR_STEP(launch_sort_and_weigh(p, workspace, s), "bin sort and gridding weights");
     MMSAR_MARK(1);
-    MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation");
+    MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation, bin sort and gridding weights");
     MMSAR_MARK(2);
     MMSAR_STEP(launch_spread(p, workspace, s), "gridding");
     MMSAR_MARK(3);

@@ -6,10 +6,10 @@
 //                   d^z = z_l - z_ref; the residual beta of Eq. 12; the
 //                   gridding position on the 2M-point oversampled aperture
 //                   grid; the compensation phase as 32-bit fixed-point turns.
-//  bin_*            counting sort of the samples by 4x4-cell bin (the
-//                   in-bin ordering is finished with the gridding weights,
-//                   in spread.cu).
-//  compensate       Eq. 11, s_hat = s exp(+j k beta), written in bin order.
+//  bin_*            counting sort of the samples by 4x4-cell bin.
+//  compensate       Eq. 11, s_hat = s exp(+j k beta) in original sample
+//                   order; the same launch finishes the binning (in-bin
+//                   sort, gridding weight records).
 //
 // Precision: FP64 is used once per sample (geometry and the phase argument
 // f0 beta / c, df beta / c reduced to [0, 1) turns and stored as uint32
@@ -344,11 +344,77 @@ cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ compensate
-// One warp per group of kCompUnroll sorted slots and one k-chunk: lane k
-// reads s[l][k] for each slot of the group (the loads of the group are
-// issued together, 256 coalesced bytes each), rotates it by
-// exp(+j 2 pi (a + k b)) and writes s_hat[kc][slot][lane].
+// ------------------------------------------------------------------ compensate and in-bin order
+// One launch with two kinds of blocks that run side by side.  The first
+// n_sort blocks finish the binning, one warp per bin: the in-bin sort and the
+// per-sample gridding records.  The other blocks apply Eq. 11 to every
+// sample.  The compensation is HBM-bound and the sort latency-bound, so the
+// sort hides under the compensation; neither reads what the other writes.
+
+// -- in-bin sort and gridding records
+// The scatter filled each bin in the arrival order of its atomics.  A rank
+// sort puts the samples of a bin of up to kSortBinCap samples in ascending
+// sample order (a fixed summation order makes the image bit-reproducible;
+// larger bins keep the arrival order, which is still correct, only the last
+// bits of the image can then vary between runs).  Then, per sample in that
+// order: its in-bin offset and sample index, and per axis w + 3 weight quads
+// (quad q = the Gaussian weights exp(-kappa (f - tap)^2) of taps q-3 .. q,
+// zero outside 0..w-1), consecutive lanes writing consecutive 16-byte entries.
+constexpr int kSortBinCap = 256;
+constexpr int kPrepWarps = 8;
+
+__device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *__restrict__ perm,
+                                   const SampleRec *__restrict__ rec, int w, float kappa, int2 *__restrict__ dd,
+                                   float4 *__restrict__ wrec, int *keys, int *sorted) {
+    const int lane = threadIdx.x & 31;
+    const int beg = offsets[b], n = offsets[b + 1] - beg;
+    if (n == 0) return;
+    int *pp = perm + beg;
+    const bool small = n <= kSortBinCap;
+    if (small) {
+        for (int i = lane; i < n; i += 32) keys[i] = pp[i];
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int ki = keys[i];
+            int rank = 0;   // #{j : key_j < key_i}; sample indices are distinct
+            for (int j = 0; j < n; ++j) rank += keys[j] < ki;
+            sorted[rank] = ki;
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) pp[i] = sorted[i];
+    }
+    const int nq = w + 3, rq = 2 * nq + 1;
+    const int total = n * rq;
+    for (int e = lane; e < total; e += 32) {
+        const int sl = e / rq, ent = e - sl * rq;
+        const int l = small ? sorted[sl] : pp[sl];
+        const SampleRec r = rec[l];
+        float4 out;
+        if (ent == 0) {
+            const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
+            dd[beg + sl] = make_int2(d, l);
+            out = make_float4(__int_as_float(d), __int_as_float(l), 0.f, 0.f);
+        } else {
+            const int q = (ent - 1) % nq;                 // quad q = taps q-3 .. q
+            const float f = (ent - 1) < nq ? r.fx : r.fy;
+            float v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int tap = q - 3 + i;
+                const float dlt = f - (float)tap;
+                v[i] = (tap >= 0 && tap < w) ? expf(-kappa * dlt * dlt) : 0.f;
+            }
+            out = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        wrec[(long long)(beg + sl) * rq + ent] = out;
+    }
+}
+
+// -- compensation (Eq. 11)
+// One warp per group of kCompUnroll samples and one k-chunk: lane k reads
+// s[l][k] for each sample of the group (the loads of the group are issued
+// together, 256 coalesced bytes each), rotates it by exp(+j 2 pi (a + k b))
+// and writes s_hat[kc][l][lane], in original sample order.
 constexpr int kCompUnroll = 4;
 
 template <int DT>
@@ -366,42 +432,60 @@ __device__ __forceinline__ float2 load_echo(const void *__restrict__ echo_v, lon
     }
 }
 
+struct PrepTailArgs {
+    // in-bin order
+    int n_bins, n_sort_blocks;
+    const int *offsets;
+    int *perm;
+    const SampleRec *rec;
+    int w;
+    float kappa;
+    int2 *dd;
+    float4 *wrec;
+    // compensation
+    const void *echo;
+    const float *scale;
+    const uint2 *phase;
+    int Nk, L, chunk_blocks;
+    int *err;
+    float2 *shat;
+};
+
 template <int DT>
-__global__ void __launch_bounds__(256) compensate_kernel(const void *__restrict__ echo_v,
-                                                         const float *__restrict__ scale_p,
-                                                         const int *__restrict__ perm,
-                                                         const uint2 *__restrict__ phase, int Nk,
-                                                         long long Lmax, const WsHeader *__restrict__ hdr,
-                                                         int *__restrict__ err, float2 *__restrict__ shat) {
-    const int n_valid = hdr->n_valid;
-    const int kc = blockIdx.y;
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArgs a) {
+    __shared__ int keys[kPrepWarps][kSortBinCap];
+    __shared__ int sorted[kPrepWarps][kSortBinCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((int)blockIdx.x < a.n_sort_blocks) {
+        const int b = blockIdx.x * kPrepWarps + warp;
+        if (b < a.n_bins)
+            sort_and_weigh_bin(b, a.offsets, a.perm, a.rec, a.w, a.kappa, a.dd, a.wrec, keys[warp], sorted[warp]);
+        return;
+    }
+    const int cblk = blockIdx.x - a.n_sort_blocks;
+    const int kc = cblk / a.chunk_blocks, bx = cblk - kc * a.chunk_blocks;
     const int k = kc * kKC + lane;
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *scale_p;
+    const int Nk = a.Nk;
+    const int warps = a.chunk_blocks * kPrepWarps;
+    const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *a.scale;
     bool bad = false;
-    for (long long g0 = ((long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * kCompUnroll; g0 < n_valid;
-         g0 += warps * kCompUnroll) {
-        int l[kCompUnroll];
+    for (int g0 = (bx * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
         uint2 ph[kCompUnroll];
         float2 v[kCompUnroll];
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
-            const long long slot = g0 + u;
-            l[u] = slot < n_valid ? __ldg(perm + slot) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kCompUnroll; ++u) {
+            const int l = g0 + u;
             v[u] = make_float2(0.f, 0.f);
             ph[u] = make_uint2(0u, 0u);
-            if (l[u] >= 0) {
-                ph[u] = __ldg(phase + l[u]);
-                if (k < Nk) v[u] = load_echo<DT>(echo_v, (long long)l[u] * Nk + k, scale);
+            if (l < a.L) {
+                ph[u] = __ldg(a.phase + l);
+                if (k < Nk) v[u] = load_echo<DT>(a.echo, (long long)l * Nk + k, scale);
             }
         }
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
-            if (l[u] < 0) continue;
+            const int l = g0 + u;
+            if (l >= a.L) continue;
             float2 out = make_float2(0.f, 0.f);
             if (k < Nk) {
                 bad |= !(isfinite(v[u].x) && isfinite(v[u].y));
@@ -413,34 +497,46 @@ __global__ void __launch_bounds__(256) compensate_kernel(const void *__restrict_
                 __sincosf(ang, &sn, &cs);
                 out = cmul(v[u], make_float2(cs, sn));
             }
-            __stcs(shat + ((long long)kc * Lmax + g0 + u) * kKC + lane, out);
+            __stcs(a.shat + ((long long)kc * a.L + l) * kKC + lane, out);
         }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, kErrNonfinite);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
 }
 
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const long long warps_needed = (p.L + kCompUnroll - 1) / kCompUnroll;
-    long long blocks = (warps_needed + 7) / 8;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    dim3 grid((unsigned)blocks, p.n_kc);
-    const int *perm = reinterpret_cast<int *>(w + p.off_perm);
-    const uint2 *ph = reinterpret_cast<uint2 *>(w + p.off_phase);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
-    float2 *shat = reinterpret_cast<float2 *>(w + p.off_shat);
+    PrepTailArgs a;
+    a.n_bins = (int)p.n_bins;
+    a.n_sort_blocks = (int)((p.n_bins + kPrepWarps - 1) / kPrepWarps);
+    a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
+    a.perm = reinterpret_cast<int *>(w + p.off_perm);
+    a.rec = reinterpret_cast<const SampleRec *>(w + p.off_rec);
+    a.w = p.w;
+    a.kappa = (float)(1.5 * kPi / p.w);
+    a.dd = reinterpret_cast<int2 *>(w + p.off_dd);
+    a.wrec = reinterpret_cast<float4 *>(w + p.off_wq);
+    a.echo = echo;
+    a.scale = scale;
+    a.phase = reinterpret_cast<const uint2 *>(w + p.off_phase);
+    a.Nk = p.shape.n_k;
+    a.L = (int)p.L;
+    const long long warps_needed = (p.L + kCompUnroll - 1) / kCompUnroll;
+    long long cb = (warps_needed + kPrepWarps - 1) / kPrepWarps;
+    if (cb > 152 * 32) cb = 152 * 32;
+    a.chunk_blocks = (int)cb;
+    a.err = &hdr->error;
+    a.shat = reinterpret_cast<float2 *>(w + p.off_shat);
+    const unsigned blocks = (unsigned)(a.n_sort_blocks + cb * p.n_kc);
     switch (p.shape.dtype) {
         case MMSAR_ECHO_C64:
-            compensate_kernel<MMSAR_ECHO_C64><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k, p.L, hdr,
-                                                                   &hdr->error, shat);
+            compensate_kernel<MMSAR_ECHO_C64><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
         case MMSAR_ECHO_F16X2_SCALED:
-            compensate_kernel<MMSAR_ECHO_F16X2_SCALED><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k,
-                                                                            p.L, hdr, &hdr->error, shat);
+            compensate_kernel<MMSAR_ECHO_F16X2_SCALED><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
         default:
-            compensate_kernel<MMSAR_ECHO_BF16X2_SCALED><<<grid, 256, 0, s>>>(echo, scale, perm, ph, p.shape.n_k,
-                                                                             p.L, hdr, &hdr->error, shat);
+            compensate_kernel<MMSAR_ECHO_BF16X2_SCALED><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
     }
     return cudaGetLastError();

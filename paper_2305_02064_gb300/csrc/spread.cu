@@ -7,13 +7,12 @@
 // cell size h = 2 pi / (2M); the sample reaches the w cells
 // u0 .. u0 + w - 1, u0 = ceil(g - w/2) (indices modulo the grid size).
 //
-// sort_and_weigh_kernel (one warp per bin): puts the samples of the bin in
-// ascending sample order (the scatter filled it in the arrival order of its
-// atomics; a fixed order makes the image bit-reproducible) and writes, per
-// sample in that order, its offset inside the 4x4-cell bin and, per axis,
-// w + 3 "quads" -- quad q holds the weights of taps q-3 .. q (zero outside
-// 0..w-1), i.e. exactly the four weights a 4-cell block needs when it starts
-// q - 3 cells after u0.
+// The per-sample records it reads (bin order; written with the in-bin sort,
+// see samples.cu): the sample's offset inside its 4x4-cell bin and original
+// index, and per axis w + 3 "quads" -- quad q holds the weights of taps
+// q-3 .. q (zero outside 0..w-1), i.e. exactly the four weights a 4-cell
+// block needs when it starts q - 3 cells after u0.  The compensated samples
+// are in original sample order.
 //
 // spread_kernel: a CTA owns a 16x8 tile of grid cells and two chunks of 32
 // frequencies; each of its 8 warps owns a 4x4 block of cells, and each lane
@@ -32,85 +31,9 @@
 
 namespace mmsar {
 
-constexpr int kSortBinCap = 256;   // bins up to this size are sorted in shared memory
-constexpr int kSortWarps = 4;
-
-__global__ void __launch_bounds__(kSortWarps * 32) sort_and_weigh_kernel(int n_bins, const int *__restrict__ offsets,
-                                                                       int *__restrict__ perm,
-                                                                       const SampleRec *__restrict__ rec, int w,
-                                                                       float kappa, int *__restrict__ dd,
-                                                                       float4 *__restrict__ wrec) {
-    __shared__ int keys[kSortWarps][kSortBinCap];
-    __shared__ int sorted[kSortWarps][kSortBinCap];
-    __shared__ SampleRec recs[kSortWarps][kSortBinCap];
-    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * kSortWarps + wb;
-    if (b >= n_bins) return;
-    const int beg = offsets[b], n = offsets[b + 1] - beg;
-    if (n == 0) return;
-    int *pp = perm + beg;
-    // rank sort: sample i goes to #{j : key_j < key_i} (sample indices are
-    // distinct); larger bins keep the arrival order (still correct, only the
-    // last bits of the image can then vary between runs)
-    const bool small = n <= kSortBinCap;
-    if (small) {
-        for (int i = lane; i < n; i += 32) keys[wb][i] = pp[i];
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const int ki = keys[wb][i];
-            int rank = 0;
-            for (int j = 0; j < n; ++j) rank += keys[wb][j] < ki;
-            sorted[wb][rank] = ki;
-        }
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const int l = sorted[wb][i];
-            pp[i] = l;
-            recs[wb][i] = rec[l];
-        }
-        __syncwarp();
-    }
-    // weight records of the bin's samples: consecutive lanes write consecutive
-    // 16-byte entries (per sample: a header, w + 3 x quads, w + 3 y quads)
-    const int nq = w + 3, rq = 2 * nq + 1;
-    const int total = n * rq;
-    for (int e = lane; e < total; e += 32) {
-        const int sl = e / rq, ent = e - sl * rq;
-        const SampleRec r = small ? recs[wb][sl] : rec[pp[sl]];
-        float4 out;
-        if (ent == 0) {
-            const int d = (r.u0 & 3) | ((r.v0 & 3) << 2);
-            dd[beg + sl] = d;
-            out = make_float4(__int_as_float(d), 0.f, 0.f, 0.f);
-        } else {
-            const int q = (ent - 1) % nq;                 // quad q = taps q-3 .. q
-            const float f = (ent - 1) < nq ? r.fx : r.fy;
-            float v[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int tap = q - 3 + i;
-                const float dlt = f - (float)tap;
-                v[i] = (tap >= 0 && tap < w) ? expf(-kappa * dlt * dlt) : 0.f;
-            }
-            out = make_float4(v[0], v[1], v[2], v[3]);
-        }
-        wrec[(long long)(beg + sl) * rq + ent] = out;
-    }
-}
-
-cudaError_t launch_sort_and_weigh(const Plan &p, void *ws, cudaStream_t s) {
-    char *w = reinterpret_cast<char *>(ws);
-    const unsigned blocks = (unsigned)((p.n_bins + kSortWarps - 1) / kSortWarps);
-    sort_and_weigh_kernel<<<blocks, kSortWarps * 32, 0, s>>>(
-        (int)p.n_bins, reinterpret_cast<const int *>(w + p.off_offsets), reinterpret_cast<int *>(w + p.off_perm),
-        reinterpret_cast<const SampleRec *>(w + p.off_rec), p.w, (float)(1.5 * kPi / p.w),
-        reinterpret_cast<int *>(w + p.off_dd), reinterpret_cast<float4 *>(w + p.off_wq));
-    return cudaGetLastError();
-}
-
 struct SpreadArgs {
-    const float2 *shat;       // [n_kc][Lmax][32], bin order
-    const int *dd;            // [Lmax] in-bin offsets du | dv << 2, bin order
+    const float2 *shat;       // [n_kc][Lmax][32], original sample order
+    const int2 *dd;           // [Lmax] (in-bin offset du | dv << 2, sample index), bin order
     const float4 *wrec;       // [Lmax][2 (w + 3) + 1]: header + x quads + y quads
     const int *offsets;       // [n_bins + 1]
     float2 *G;                // [n_kc][mry][mrx][32]
@@ -234,12 +157,13 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
                 bool rel = false;
                 int4 ent = make_int4(0, 0, 0, 0);
                 if (my < end) {
-                    const int d = __ldg(a.dd + my);
+                    const int2 ds = __ldg(a.dd + my);
+                    const int d = ds.x;
                     const int ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
                     const int rv = 4 * dbv - (d >> 2);
                     rel = ru < a.w && rv < a.w;
                     const int base = my * rq + 1;         // the sample's x quads, then its y quads
-                    ent = make_int4(base + ru + 3, base + nq + rv + 3, my, 0);
+                    ent = make_int4(base + ru + 3, base + nq + rv + 3, ds.y, 0);
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, rel);
                 if (n + __popc(mask) > kListCap) {   // keep the list within its buffer
@@ -270,7 +194,7 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
     SpreadArgs a;
     a.shat = reinterpret_cast<const float2 *>(w + p.off_shat);
-    a.dd = reinterpret_cast<const int *>(w + p.off_dd);
+    a.dd = reinterpret_cast<const int2 *>(w + p.off_dd);
     a.wrec = reinterpret_cast<const float4 *>(w + p.off_wq);
     a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
     a.G = reinterpret_cast<float2 *>(w + p.off_G);
