@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace mmsar {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -183,6 +185,114 @@ __host__ __device__ constexpr int fft_pitch(int C) { return C >= 32 ? C : C + 1;
 template <int L, int C, int NT, int SIGN, int P = fft_pitch(C)>
 __device__ __forceinline__ void smem_fft(float2 *buf, const float2 *tw) {
     FftRun<L, 1, C, P, NT, SIGN>::run(buf, tw);
+}
+
+// ---------------------------------------------------------------- register DFTs
+// N-point DFTs held entirely in one thread's registers (N = 2 .. 64), with
+// every internal twiddle a compile-time constant.  N > 8 splits as
+// N = R1 x N2 (R1 = 4 for N = 16, else 8): R1-point DFTs over the N2
+// decimated subsequences, twiddles exp(SIGN 2 pi i n2 k1 / N), then N2-point
+// DFTs, X[k1 + R1 k2] = sum_n2 W_N2^(n2 k2) W_N^(n2 k1) sum_n1 x[n2 + N2 n1] W_R1^(n1 k1).
+
+// cos / sin of 2 pi m / n (exact multiples of a turn), evaluated at compile
+// time: reduce to [0, pi/4] by the octant symmetries, then Taylor series.
+__host__ __device__ constexpr double ct_sin_series(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_cos_series(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 14; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+// (cos, sin)(2 pi m / n) for m in [0, n): eighth-turn octants o = 0..7
+__host__ __device__ constexpr double ct_cos_turn(int m, int n) {
+    const double pi = 3.141592653589793238462643383279502884;
+    const int e = 8 * m / n;                      // octant
+    const double r = (double)(8 * m - e * n) / n; // position inside it, [0, 1)
+    const double a = (pi / 4.0) * r, b = (pi / 4.0) * (1.0 - r);
+    switch (e) {
+        case 0: return ct_cos_series(a);
+        case 1: return ct_sin_series(b);
+        case 2: return -ct_sin_series(a);
+        case 3: return -ct_cos_series(b);
+        case 4: return -ct_cos_series(a);
+        case 5: return -ct_sin_series(b);
+        case 6: return ct_sin_series(a);
+        default: return ct_cos_series(b);
+    }
+}
+__host__ __device__ constexpr double ct_sin_turn(int m, int n) {
+    // sin(theta) = cos(theta - pi/2): shift by a quarter turn
+    return ct_cos_turn(((4 * m - n) % (4 * n) + 4 * n) % (4 * n), 4 * n);
+}
+
+// a * exp(SIGN 2 pi i M / N), M and N compile-time
+template <int N, int M, int SIGN>
+__device__ __forceinline__ float2 twiddle_ct(float2 a) {
+    constexpr int m = ((M % N) + N) % N;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (2 * m == N) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (4 * m == N) {
+        return mul_si<SIGN>(a);
+    } else if constexpr (4 * m == 3 * N) {
+        return mul_si<-SIGN>(a);
+    } else {
+        constexpr float c = (float)ct_cos_turn(m, N);
+        constexpr float s = (float)(SIGN * ct_sin_turn(m, N));
+        return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+    }
+}
+
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>()), ...);
+}
+// f(std::integral_constant<int, i>) for i = 0 .. N-1, unrolled at compile time
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>());
+}
+
+// In-place DFT of v[0..N-1] (natural order in and out).
+template <int N, int SIGN>
+__device__ __forceinline__ void reg_dft(float2 *v) {
+    if constexpr (N <= 8) {
+        dft_r<N, SIGN>(v);
+    } else {
+        constexpr int R1 = N == 16 ? 4 : 8;
+        constexpr int N2 = N / R1;
+        float2 t[N];
+        static_for<N2>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            float2 a[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[n2 + N2 * n1];
+            dft_r<R1, SIGN>(a);
+            static_for<R1>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                t[n2 * R1 + k1] = twiddle_ct<N, n2 * k1, SIGN>(a[k1]);
+            });
+        });
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            float2 b[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) b[n2] = t[n2 * R1 + k1];
+            reg_dft<N2, SIGN>(b);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) v[k1 + R1 * k2] = b[k2];
+        }
+    }
 }
 
 }  // namespace mmsar

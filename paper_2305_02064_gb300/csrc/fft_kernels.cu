@@ -94,6 +94,120 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     }
 }
 
+// Register kernel (L = 64 .. 1024): the same tile of L rows x C columns as a
+// two-step transform, L = N1 x N2.  Step 1: a thread takes input rows
+// n2 + N2 n1 (n1 = 0 .. N1-1) of one column straight from global memory into
+// registers (all its loads in flight at once), runs the N1-point DFT,
+// multiplies by exp(SIGN 2 pi i n2 k1 / L) and writes the N1 results to a
+// transpose buffer in shared memory.  Step 2: a thread takes the N2 values
+// of one (k1, column), runs the N2-point DFT and stores the kept outputs
+// X[k1 + N1 k2] directly.  Shared memory is written once and read once.
+__host__ __device__ constexpr int reg_fft_n1(int L) { return L <= 128 ? 8 : (L <= 512 ? 16 : 32); }
+__host__ __device__ constexpr int reg_fft_pitch(int L) {
+    return reg_fft_n1(L) * fft_cols(L) + (fft_cols(L) < 32 ? 8 : 0);
+}
+
+template <int L, int SIGN>
+__global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a) {
+    constexpr int N1 = reg_fft_n1(L), N2 = L / N1;
+    constexpr int C = fft_cols(L);
+    constexpr int IT1 = N2 * C / kFftThreads;   // step-1 columns per thread (N1 values each)
+    constexpr int IT2 = N1 * C / kFftThreads;   // step-2 columns per thread (N2 values each)
+    static_assert(IT1 >= 1 && IT2 >= 1 && (N2 * C) % kFftThreads == 0 && (N1 * C) % kFftThreads == 0,
+                  "tile does not split evenly over the threads");
+    constexpr int YP = reg_fft_pitch(L);   // pitch of one n2 row of the transpose buffer (complex)
+    extern __shared__ __align__(16) float2 smem[];
+    float2 *y = smem;              // [N2][YP]: y[n2][k1 C + c]
+    float2 *tw = smem + N2 * YP;   // [L]: exp(SIGN 2 pi i t / L)
+    const int tid = threadIdx.x;
+    const int nchunks = (a.ncols + C - 1) / C;
+    const int chunk = blockIdx.x % nchunks;
+    const int t2 = blockIdx.x / nchunks;
+    const int t1 = blockIdx.y;
+    if (a.tile_win) {
+        const int len = a.tile_win[1];
+        if (len < a.nt2) {
+            int d = (t2 - a.tile_win[0]) % a.nt2;
+            if (d < 0) d += a.nt2;
+            if (d >= len) return;   // a row that is known to be zero: nothing to do
+        }
+    }
+    int wlo = 0, wlen = a.n_in;
+    if (a.in_win) {
+        wlo = a.in_win[0];
+        wlen = a.in_win[1];
+    }
+    const int c0 = chunk * C;
+    const int cw = min(C, a.ncols - c0);
+    const float2 *in = a.in + t1 * a.in_t1 + t2 * a.in_t2 + c0;
+    float2 *out = a.out + t1 * a.out_t1 + t2 * a.out_t2 + c0;
+
+    // step 1: loads (zero outside the input rows and the occupied window)
+    float2 v[IT1][N1];
+#pragma unroll
+    for (int it = 0; it < IT1; ++it) {
+        const int item = tid + it * kFftThreads;
+        const int c = item % C, n2 = item / C;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const int r = (n2 + N2 * n1 - a.in_shift) & (L - 1);
+            int d = r - wlo;
+            if (d < 0) d += a.n_in;
+            const bool live = r < a.n_in && c < cw && d < wlen;
+            v[it][n1] = live ? in[(long long)r * a.in_row + c] : make_float2(0.f, 0.f);
+        }
+    }
+    fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IT1; ++it) {
+        const int item = tid + it * kFftThreads;
+        const int c = item % C, n2 = item / C;
+        reg_dft<N1, SIGN>(v[it]);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1)
+            y[n2 * YP + k1 * C + c] = k1 == 0 ? v[it][0] : cmul(v[it][k1], tw[(n2 * k1) & (L - 1)]);
+    }
+    __syncthreads();
+
+    // step 2: N2-point DFTs and the stores of the kept rows
+    const int half = a.n_out / 2;
+#pragma unroll
+    for (int it = 0; it < IT2; ++it) {
+        const int item = tid + it * kFftThreads;
+        const int c = item % C, k1 = item / C;
+        float2 b[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) b[n2] = y[n2 * YP + k1 * C + c];
+        reg_dft<N2, SIGN>(b);
+        if (c < cw) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int i = k1 + N1 * k2;             // FFT output index
+                const int f = i < L / 2 ? i : i - L;    // signed frequency
+                const int o = f + half;
+                if (o >= 0 && o < a.n_out) {
+                    float sc = a.scale;
+                    if (a.gauss_tau > 0.f) sc *= __expf((float)(f * f) * a.gauss_tau);
+                    out[(long long)o * a.out_row + c] = make_float2(b[k2].x * sc, b[k2].y * sc);
+                }
+            }
+        }
+    }
+}
+
+template <int L, int SIGN>
+static cudaError_t launch_reg(const ColumnFFT &a, cudaStream_t s) {
+    constexpr int C = fft_cols(L);
+    const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2);
+    cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN>, smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (a.ncols + C - 1) / C;
+    dim3 grid((unsigned)(a.nt2 * nchunks), (unsigned)a.nt1);
+    column_fft_reg_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int L, int SIGN, int VEC>
 static cudaError_t launch_LV(const ColumnFFT &a, cudaStream_t s) {
     constexpr int C = fft_cols(L);
@@ -120,11 +234,11 @@ static cudaError_t dispatch(const ColumnFFT &a, cudaStream_t s) {
     switch (a.L) {
         case 16: return launch_L<16, SIGN>(a, s);
         case 32: return launch_L<32, SIGN>(a, s);
-        case 64: return launch_L<64, SIGN>(a, s);
-        case 128: return launch_L<128, SIGN>(a, s);
-        case 256: return launch_L<256, SIGN>(a, s);
-        case 512: return launch_L<512, SIGN>(a, s);
-        case 1024: return launch_L<1024, SIGN>(a, s);
+        case 64: return launch_reg<64, SIGN>(a, s);
+        case 128: return launch_reg<128, SIGN>(a, s);
+        case 256: return launch_reg<256, SIGN>(a, s);
+        case 512: return launch_reg<512, SIGN>(a, s);
+        case 1024: return launch_reg<1024, SIGN>(a, s);
         case 2048: return launch_L<2048, SIGN>(a, s);
         default: return cudaErrorInvalidValue;
     }
