@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
     extern __shared__ __align__(16) float2 smem[];
     float2 *y = smem;              // [N2][YP]: y[n2][k1 C + c]
     float2 *tw = smem + N2 * YP;   // [L]: exp(SIGN 2 pi i t / L)
+    float *dscale = reinterpret_cast<float *>(tw + L);   // [n_out <= L]: output row scales
     const int tid = threadIdx.x;
     const int nchunks = (a.ncols + C - 1) / C;
     const int chunk = blockIdx.x % nchunks;
@@ -142,22 +143,30 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
     const float2 *in = a.in + t1 * a.in_t1 + t2 * a.in_t2 + c0;
     float2 *out = a.out + t1 * a.out_t1 + t2 * a.out_t2 + c0;
 
-    // step 1: loads (zero outside the input rows and the occupied window)
+    // step 1: loads (zero outside the occupied window); all L rows are input
+    // rows here (n_in = L), so row r = (f - in_shift) mod L and the window
+    // test is (r - wlo) mod L < wlen
     float2 v[IT1][N1];
 #pragma unroll
     for (int it = 0; it < IT1; ++it) {
         const int item = tid + it * kFftThreads;
         const int c = item % C, n2 = item / C;
+        const int r0 = n2 - a.in_shift, d0 = r0 - wlo;
+        const bool cok = c < cw;
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
-            const int r = (n2 + N2 * n1 - a.in_shift) & (L - 1);
-            int d = r - wlo;
-            if (d < 0) d += a.n_in;
-            const bool live = r < a.n_in && c < cw && d < wlen;
+            const int r = (r0 + N2 * n1) & (L - 1);
+            const bool live = cok && ((d0 + N2 * n1) & (L - 1)) < wlen;
             v[it][n1] = live ? in[(long long)r * a.in_row + c] : make_float2(0.f, 0.f);
         }
     }
     fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
+    // scale of each kept output row: scale * exp(f^2 tau) (Gaussian deconvolution)
+    const int half = a.n_out / 2;
+    for (int o = tid; o < a.n_out; o += kFftThreads) {
+        const int f = o - half;
+        dscale[o] = a.gauss_tau > 0.f ? a.scale * expf((float)(f * f) * a.gauss_tau) : a.scale;
+    }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < IT1; ++it) {
@@ -171,7 +180,6 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
     __syncthreads();
 
     // step 2: N2-point DFTs and the stores of the kept rows
-    const int half = a.n_out / 2;
 #pragma unroll
     for (int it = 0; it < IT2; ++it) {
         const int item = tid + it * kFftThreads;
@@ -183,13 +191,11 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
         if (c < cw) {
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) {
-                const int i = k1 + N1 * k2;             // FFT output index
-                const int f = i < L / 2 ? i : i - L;    // signed frequency
-                const int o = f + half;
+                const int i = k1 + N1 * k2;                      // FFT output index
+                const int o = (i < L / 2 ? i : i - L) + half;    // signed frequency + half
                 if (o >= 0 && o < a.n_out) {
-                    float sc = a.scale;
-                    if (a.gauss_tau > 0.f) sc *= __expf((float)(f * f) * a.gauss_tau);
-                    out[(long long)o * a.out_row + c] = make_float2(b[k2].x * sc, b[k2].y * sc);
+                    const float sc = dscale[o];
+                    out[(long long)o * a.out_row + c] = fmul2(make_float2(sc, sc), b[k2]);
                 }
             }
         }
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
 template <int L, int SIGN>
 static cudaError_t launch_reg(const ColumnFFT &a, cudaStream_t s) {
     constexpr int C = fft_cols(L);
-    const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2);
+    const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2) + L * sizeof(float);
     cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN>, smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (a.ncols + C - 1) / C;
@@ -234,11 +240,11 @@ static cudaError_t dispatch(const ColumnFFT &a, cudaStream_t s) {
     switch (a.L) {
         case 16: return launch_L<16, SIGN>(a, s);
         case 32: return launch_L<32, SIGN>(a, s);
-        case 64: return launch_reg<64, SIGN>(a, s);
-        case 128: return launch_reg<128, SIGN>(a, s);
-        case 256: return launch_reg<256, SIGN>(a, s);
-        case 512: return launch_reg<512, SIGN>(a, s);
-        case 1024: return launch_reg<1024, SIGN>(a, s);
+        case 64: return a.n_in == 64 ? launch_reg<64, SIGN>(a, s) : launch_L<64, SIGN>(a, s);
+        case 128: return a.n_in == 128 ? launch_reg<128, SIGN>(a, s) : launch_L<128, SIGN>(a, s);
+        case 256: return a.n_in == 256 ? launch_reg<256, SIGN>(a, s) : launch_L<256, SIGN>(a, s);
+        case 512: return a.n_in == 512 ? launch_reg<512, SIGN>(a, s) : launch_L<512, SIGN>(a, s);
+        case 1024: return a.n_in == 1024 ? launch_reg<1024, SIGN>(a, s) : launch_L<1024, SIGN>(a, s);
         case 2048: return launch_L<2048, SIGN>(a, s);
         default: return cudaErrorInvalidValue;
     }

@@ -157,7 +157,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_perm = take(sizeof(int) * L);
     p.off_dd = take(sizeof(int2) * L);
     p.off_wq = take(sizeof(float4) * (size_t)(2 * p.w + 7) * L);
-    p.off_shat = take(sizeof(float2) * (size_t)p.n_kc * L * kKC);
+    p.off_shat = take(sizeof(float2) * (size_t)((p.n_kc + 1) / 2) * L * 2 * kKC);   // 64-frequency groups
     const size_t G = sizeof(float2) * (size_t)p.n_kc * p.mry * p.mrx * kKC;
     const size_t S = sizeof(float2) * (size_t)p.mx * p.my * p.nkp;
     const size_t B = sizeof(float2) * (size_t)p.mx * g.ny * g.nz;

@@ -411,10 +411,13 @@ __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *
 }
 
 // -- compensation (Eq. 11)
-// One warp per group of kCompUnroll samples and one k-chunk: lane k reads
-// s[l][k] for each sample of the group (the loads of the group are issued
-// together, 256 coalesced bytes each), rotates it by exp(+j 2 pi (a + k b))
-// and writes s_hat[kc][l][lane], in original sample order.
+// One warp per group of kCompUnroll samples and one 64-frequency group g:
+// lane l reads s[l][64 g + l] and s[l][64 g + 32 + l] for each sample of the
+// group (the loads of the group are issued together, 256 coalesced bytes
+// each), rotates them by exp(+j 2 pi (a + k b)) and writes s_hat in original
+// sample order with the two halves of the group side by side,
+// s_hat[g][l][0..63] (512 contiguous bytes per sample; frequencies past Nk
+// are written as zero).
 constexpr int kCompUnroll = 4;
 
 template <int DT>
@@ -463,41 +466,46 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
         return;
     }
     const int cblk = blockIdx.x - a.n_sort_blocks;
-    const int kc = cblk / a.chunk_blocks, bx = cblk - kc * a.chunk_blocks;
-    const int k = kc * kKC + lane;
+    const int g = cblk / a.chunk_blocks, bx = cblk - g * a.chunk_blocks;
     const int Nk = a.Nk;
     const int warps = a.chunk_blocks * kPrepWarps;
     const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *a.scale;
     bool bad = false;
     for (int g0 = (bx * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
         uint2 ph[kCompUnroll];
-        float2 v[kCompUnroll];
+        float2 v[kCompUnroll][2];
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
             const int l = g0 + u;
-            v[u] = make_float2(0.f, 0.f);
-            ph[u] = make_uint2(0u, 0u);
-            if (l < a.L) {
-                ph[u] = __ldg(a.phase + l);
-                if (k < Nk) v[u] = load_echo<DT>(a.echo, (long long)l * Nk + k, scale);
+            ph[u] = l < a.L ? __ldg(a.phase + l) : make_uint2(0u, 0u);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 64 * g + 32 * h + lane;
+                v[u][h] = (l < a.L && k < Nk) ? load_echo<DT>(a.echo, (long long)l * Nk + k, scale)
+                                              : make_float2(0.f, 0.f);
             }
         }
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
             const int l = g0 + u;
             if (l >= a.L) continue;
-            float2 out = make_float2(0.f, 0.f);
-            if (k < Nk) {
-                bad |= !(isfinite(v[u].x) && isfinite(v[u].y));
-                const uint32_t turns = ph[u].x + (uint32_t)k * ph[u].y;            // exact mod 2^32
-                // the angle is already reduced to [-pi, pi): the hardware sine and
-                // cosine (absolute error ~4e-7 there) are accurate enough
-                const float ang = (float)(int32_t)turns * 1.4629180792671596e-09f;  // 2 pi turns / 2^32
-                float sn, cs;
-                __sincosf(ang, &sn, &cs);
-                out = cmul(v[u], make_float2(cs, sn));
+            float2 *dst = a.shat + ((long long)g * a.L + l) * (2 * kKC) + lane;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 64 * g + 32 * h + lane;
+                float2 out = make_float2(0.f, 0.f);
+                if (k < Nk) {
+                    bad |= !(isfinite(v[u][h].x) && isfinite(v[u][h].y));
+                    const uint32_t turns = ph[u].x + (uint32_t)k * ph[u].y;            // exact mod 2^32
+                    // the angle is already reduced to [-pi, pi): the hardware sine and
+                    // cosine (absolute error ~4e-7 there) are accurate enough
+                    const float ang = (float)(int32_t)turns * 1.4629180792671596e-09f;  // 2 pi turns / 2^32
+                    float sn, cs;
+                    __sincosf(ang, &sn, &cs);
+                    out = cmul(v[u][h], make_float2(cs, sn));
+                }
+                __stcs(dst + 32 * h, out);
             }
-            __stcs(a.shat + ((long long)kc * a.L + l) * kKC + lane, out);
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
@@ -527,7 +535,7 @@ cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const f
     a.chunk_blocks = (int)cb;
     a.err = &hdr->error;
     a.shat = reinterpret_cast<float2 *>(w + p.off_shat);
-    const unsigned blocks = (unsigned)(a.n_sort_blocks + cb * p.n_kc);
+    const unsigned blocks = (unsigned)(a.n_sort_blocks + cb * ((p.n_kc + 1) / 2));
     switch (p.shape.dtype) {
         case MMSAR_ECHO_C64:
             compensate_kernel<MMSAR_ECHO_C64><<<blocks, kPrepWarps * 32, 0, s>>>(a);

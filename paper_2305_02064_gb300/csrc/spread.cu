@@ -32,7 +32,7 @@
 namespace mmsar {
 
 struct SpreadArgs {
-    const float2 *shat;       // [n_kc][Lmax][32], original sample order
+    const float2 *shat;       // [n_kc / 2][Lmax][64], original sample order
     const int2 *dd;           // [Lmax] (in-bin offset du | dv << 2, sample index), bin order
     const float4 *wrec;       // [Lmax][2 (w + 3) + 1]: header + x quads + y quads
     const int *offsets;       // [n_bins + 1]
@@ -59,16 +59,16 @@ constexpr int kSpreadThreads = 256;   // 8 warps: a 16 x 8-cell tile
 constexpr int kListCap = 192;
 constexpr int kSpreadChunks = 2;   // frequency chunks of 32 per CTA   // relevant samples listed per warp before they are applied
 
-template <int NF, int NS, int MINB>
+template <int NS, int MINB>
 __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs a) {
     // per warp: (x-quad index, y-quad index, sample index) of each listed sample
     __shared__ int4 lists[kSpreadThreads / 32][kListCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx >> 4;
-    // a CTA covers NF frequency chunks (a lane holds NF frequencies); the
-    // chunk group varies fastest, so the groups of one tile run together and
-    // share the tile's weight records in L2
-    const int n_kg = (a.n_kc + NF - 1) / NF;
+    // a CTA covers one 64-frequency group (two chunks of 32); lane l holds
+    // frequencies 2l and 2l + 1 of the group.  The group varies fastest, so
+    // the groups of one tile run together and share its weight records in L2
+    const int n_kg = (a.n_kc + 1) / 2;
     const int kg = blockIdx.x % n_kg;
     const int tile = blockIdx.x / n_kg;
     // tiles outside the occupied window stay unwritten: the FFT along x'
@@ -80,25 +80,18 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
     const int V = (tile / tiles_x) * 8 + (warp >> 2) * 4;
     const int rq = 2 * (a.w + 3) + 1;
     const int nq = a.w + 3;
-    // chunks past the last one (odd chunk count) repeat it and are not stored
-    int kc[NF];
+    float4 acc[4][4];   // (re, im) of frequency 2l, then of 2l + 1
 #pragma unroll
-    for (int f = 0; f < NF; ++f) kc[f] = min(kg * NF + f, a.n_kc - 1);
-    float2 acc[NF][4][4];
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[f][j][i] = make_float2(0.f, 0.f);
-    const float2 *sh = a.shat + (long long)kc[0] * a.Lmax * kKC + lane;
-    const long long kstride = NF > 1 ? (long long)(kc[NF - 1] - kc[0]) * a.Lmax * kKC : 0;
+        for (int i = 0; i < 4; ++i) acc[j][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // s_hat group kg: [Lmax][64] complex, 16 bytes per lane per sample
+    const float4 *sh = reinterpret_cast<const float4 *>(a.shat) + (long long)kg * a.Lmax * 32 + lane;
     int4 *list = lists[warp];
 
     // one listed sample in flight: its x and y weight quads and its values
     struct Stage {
-        float4 x, y;
-        float2 v[NF];
+        float4 x, y, v;
     };
     // apply the listed samples through an NS-deep pipeline: the loads of
     // entry i + NS are issued as soon as entry i has been accumulated
@@ -108,22 +101,23 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
             const int4 e = list[i];
             q.x = __ldg(a.wrec + e.x);
             q.y = __ldg(a.wrec + e.y);
-            const float2 *p = sh + (e.z << 5);
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q.v[f] = __ldg(p + f * kstride);
+            q.v = __ldg(sh + (e.z << 5));
         };
         auto consume = [&](const Stage &q) {
             const float wx[4] = {q.x.x, q.x.y, q.x.z, q.x.w};
             const float wy[4] = {q.y.x, q.y.y, q.y.z, q.y.w};
+            const float2 v0 = make_float2(q.v.x, q.v.y), v1 = make_float2(q.v.z, q.v.w);
             // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float2 wyj = make_float2(wy[j], wy[j]);
+                const float2 t0 = fmul2(wyj, v0), t1 = fmul2(wyj, v1);
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const float2 t = fmul2(wyj, q.v[f]);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[f][j][i] = ffma2(make_float2(wx[i], wx[i]), t, acc[f][j][i]);
+                for (int i = 0; i < 4; ++i) {
+                    const float2 wxi = make_float2(wx[i], wx[i]);
+                    const float2 a0 = ffma2(wxi, t0, make_float2(acc[j][i].x, acc[j][i].y));
+                    const float2 a1 = ffma2(wxi, t1, make_float2(acc[j][i].z, acc[j][i].w));
+                    acc[j][i] = make_float4(a0.x, a0.y, a1.x, a1.y);
                 }
             }
         };
@@ -179,14 +173,15 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
     }
     __syncwarp();
     apply(n);
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        if (f > 0 && kg * NF + f >= a.n_kc) break;
-        float2 *g = a.G + (long long)kc[f] * a.mry * a.mrx * kKC;
+    // lanes 0..15 hold chunk 2 kg, lanes 16..31 chunk 2 kg + 1 (absent when
+    // the chunk count is odd): 16 bytes per lane, 256 contiguous bytes per chunk
+    const int kc = 2 * kg + (lane >> 4);
+    if (kc < a.n_kc) {
+        float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + (lane & 15);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC + lane] = acc[f][j][i];
+            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2)] = acc[j][i];
     }
 }
 
@@ -207,10 +202,10 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
-    // two frequency chunks per CTA (a lane holds two frequencies), three
+    // a 64-frequency group per CTA (a lane holds two frequencies), three
     // listed samples in flight, two CTAs per SM
     const unsigned tiles = (unsigned)((p.mrx / 16) * (p.mry / 8));
-    spread_kernel<kSpreadChunks, 3, 2><<<tiles * ((p.n_kc + kSpreadChunks - 1) / kSpreadChunks), kSpreadThreads, 0, s>>>(a);
+    spread_kernel<3, 2><<<tiles * ((p.n_kc + 1) / 2), kSpreadThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

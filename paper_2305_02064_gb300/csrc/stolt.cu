@@ -144,11 +144,19 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                 for (int jb = J_lo; jb <= J_hi; jb += 32) {
                     const int j = jb + lane;
                     if (j <= J_hi) {
+                        // windows start in non-decreasing order: the ones that
+                        // reach point j start in [j - WR + 1, j], a run of lanes
+                        // from the first start >= j - WR + 1 (binary search)
+                        int lo = 0, hi = nact;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (jw[mid] < j - WR + 1) lo = mid + 1; else hi = mid;
+                        }
                         float2 sum = make_float2(0.f, 0.f);
-                        for (int l2 = 0; l2 < nact; ++l2) {
+                        for (int l2 = lo; l2 < nact; ++l2) {
                             const int o = j - jw[l2];
-                            if (o < 0) break;          // windows start in non-decreasing order
-                            if (o < WR) sum = cadd(sum, wb[l2 * WP + o]);
+                            if (o < 0) break;
+                            sum = cadd(sum, wb[l2 * WP + o]);
                         }
                         float2 &gref = grid[(j & (MRZ - 1)) * GP + warp];
                         gref = cadd(gref, sum);
