@@ -48,7 +48,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["realistic", "tiny", "large", "batch", "serve"], default="realistic")
+    ap.add_argument("--workload", choices=["realistic", "tiny", "large", "batch", "serve", "psf"], default="realistic")
+    ap.add_argument("--compensate", type=int, choices=[0, 1, 2], default=1,
+                    help="1: Eq. 11-12 (the paper's residual), 2: Eq. 5 at the scene centre, 0: none (ablation)")
     ap.add_argument("--mix", type=int, default=64, help="scans in the batched mix")
     ap.add_argument("--requests", type=int, default=256, help="requests in the serving run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -284,7 +286,7 @@ def run_ours(args, dist):
     dev = torch.device(f"cuda:{dist.local_rank}")
     torch.cuda.set_device(dev)
     scan = make_scan(args.workload, dist.rank)
-    plan = mm.Plan.for_scan(scan)
+    plan = mm.Plan.for_scan(scan, compensate=args.compensate)
     stream = torch.cuda.Stream(device=dev)
     ws = plan.new_workspace(dev)
     vol = plan.new_volume(dev)
@@ -384,12 +386,12 @@ def run_ours(args, dist):
     return res, scan, vol
 
 
-def cpu_baseline(scan, vol_gpu):
+def cpu_baseline(scan, vol_gpu, compensate=1):
     """The FP64 oracle (rma_fast) on the whole scan, timed on the host cores;
     also the NMSE of the GPU volume against it."""
     import numpy as np
     from oracle import rma
-    su = rma.setup_from(scan)
+    su = rma.setup_from(scan, compensate=compensate)
     t0 = time.time()
     ref = rma.rma_fast(su)
     dt = time.time() - t0
@@ -415,7 +417,7 @@ def storage_comparison(scan, vol_fp32, args):
     out = {}
     vols = {"fp32": vol_fp32.cpu().numpy()}
     for dt in ("bf16", "f16"):
-        plan = mm.Plan.for_scan(scan, dtype=dt)
+        plan = mm.Plan.for_scan(scan, dtype=dt, compensate=args.compensate)
         q, sc = mm.quantize_echo(echo, dt)
         ws, vol = plan.new_workspace(dev), plan.new_volume(dev)
         for _ in range(3):
@@ -433,7 +435,7 @@ def storage_comparison(scan, vol_fp32, args):
         vols[dt] = vol.cpu().numpy()
         del ws, q
     t0 = time.time()
-    ref = rma.rma_fast(rma.setup_from(scan), w=12)
+    ref = rma.rma_fast(rma.setup_from(scan, compensate=args.compensate), w=12)
     oracle_s = time.time() - t0
     for k, v in vols.items():
         out.setdefault(k, {})["nmse_vs_oracle"] = float(rma.nmse(v, ref))
@@ -450,7 +452,7 @@ def run_reference(args, dist):
     if dist.rank != 0:
         return None
     scan = make_scan(args.workload, 0)
-    su = rma.setup_from(scan)
+    su = rma.setup_from(scan, compensate=args.compensate)
     nk = su.n_k
     ks = max(1, nk // 8)
     times = []
@@ -591,6 +593,64 @@ def run_serve(args, dist):
             "forms": out, "worst_nmse_served_vs_plain_fp32": worst}
 
 
+# ----------------------------------------------------------------------------- PSF study (Sec. V-A)
+PSF_DZ = (0.0, 0.05, 0.10, 0.15, 0.20)
+
+
+def run_psf(args, dist):
+    """The point-spread study of Sec. V-A: a linear-track scan of one point
+    target at 0.5 m with the samples up to dz_max off the reference plane,
+    imaged on the GPU without compensation, with Eq. 7's residual and with
+    Eq. 5's at the scene centre; per case the -3 dB main-lobe widths, the
+    peak's offset and amplitude, and the NMSE against the FP64 oracle of the
+    same mode."""
+    import numpy as np
+    import torch
+    import paper_2305_02064_gb300 as mm
+    from paper_2305_02064_gb300 import quality
+    from oracle import rma
+    import synth
+    dev = torch.device(f"cuda:{dist.local_rank}")
+    rows = []
+    ideal = None
+    t_img = []
+    for dz in PSF_DZ:
+        sc = synth.psf_track(dz)
+        echo = torch.from_numpy(np.ascontiguousarray(sc.echo)).to(dev)
+        pos, tx, rx = (torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev) for a in (sc.pos, sc.tx, sc.rx))
+        for mode in (0, 1, 2):
+            plan = mm.Plan.for_scan(sc, z_ref=0.0, compensate=mode)
+            ws = plan.new_workspace(dev)
+            vol = plan.new_volume(dev)
+            for _ in range(3):
+                plan.image(ws, echo, pos, tx, rx, vol)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                plan.image(ws, echo, pos, tx, rx, vol)
+            e1.record()
+            torch.cuda.synchronize()
+            t_img.append(e0.elapsed_time(e1) / 10)
+            plan.poll_error(ws)
+            got = vol.cpu().numpy()
+            m = quality.psf_metrics(got, sc.grid, sc.scatterers[0])
+            su = rma.setup_from(sc, z_ref=0.0, compensate=mode, Mx=plan.mx, My=plan.my)
+            m["nmse_vs_oracle"] = float(rma.nmse(got, rma.rma_fast(su, w=16)))
+            if dz == 0.0 and mode == 1:
+                ideal = m["peak"]
+            m.update({"dz_max_cm": dz * 100, "compensate": mode})
+            rows.append({k: (float(f"{float(v):.4g}") if isinstance(v, (float, np.floating)) else v) for k, v in m.items()})
+    for r in rows:
+        r["peak_rel_planar"] = float(f"{r['peak'] / ideal:.4g}")
+    return {"metric": "point-spread main-lobe widths vs largest plane deviation (Sec. V-A study)",
+            "value": None, "unit": "mm", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "linear 2Tx x 4Rx track, 256 positions over y' in [-12.5, 12.5] cm, Nk=64, "
+                                   "point at (0, 0, 0.5 m), y-z image 256 x 64 at 1 x 2.5 mm",
+                       "dz_max_cm": [d * 100 for d in PSF_DZ],
+                       "compensate": {"0": "none", "1": "Eq. 7 residual (paper)", "2": "Eq. 5 at the scene centre"}},
+            "ms_per_image_mean": round(float(np.mean(t_img)), 4), "rows": rows}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -601,6 +661,12 @@ def main():
         dist.close()
         return 0
     dist = Dist(want_cuda=True)
+    if args.workload == "psf":
+        res = run_psf(args, dist) if dist.rank == 0 else None
+        if res is not None:
+            print(json.dumps(res))
+        dist.close()
+        return 0
     if args.workload in ("batch", "serve"):
         res = (run_batch if args.workload == "batch" else run_serve)(args, dist)
         if dist.rank == 0:
@@ -611,7 +677,7 @@ def main():
     if args.workload == "large" and dist.rank == 0 and dist.world == 1:
         res["storage_comparison"] = storage_comparison(scan, vol, args)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cb, acc = cpu_baseline(scan, vol)
+        cb, acc = cpu_baseline(scan, vol, args.compensate)
         res["cpu_baseline"] = cb
         res["accuracy"] = acc
     if dist.rank == 0:

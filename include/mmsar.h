@@ -85,7 +85,11 @@ typedef struct {
 typedef struct {
     double z_ref;      /* virtual plane Z0 (Eq. 4); NaN => mean of z_l over samples    */
     double z_scene;    /* scene depth for the MIMO term of Eq. 12; NaN => grid z centre */
-    int compensate;    /* 1 = Eq. 11-12 applied (paper); 0 = beta = 0 (RMA ablation)   */
+    int compensate;    /* 1 = Eq. 11-12 applied (paper: Eq. 7's on-axis residual);      *
+                        * 2 = Eq. 11 with the residual of Eq. 5 evaluated at the scene   *
+                        *     centre (x_c, y_c, z_scene) for each virtual element, i.e.   *
+                        *     with the off-axis terms Eq. 7 drops;                       *
+                        * 0 = beta = 0 (RMA ablation).  Other values: INVALID_ARG.       */
     double nufft_tol;  /* Gaussian gridding accuracy per transform; <= 0 => 1e-3        */
     int mx, my;        /* spectral grid (power of two >= nx, ny, 16..1024); 0 => auto  */
 } mmsar_options;

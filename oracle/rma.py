@@ -78,7 +78,7 @@ class Setup:
     nz: int
     z_ref: float
     z_scene: float
-    compensate: bool
+    compensate: int         # 0 none, 1 Eq. 7 residual (paper), 2 Eq. 5 at the scene centre
     Mx: int
     My: int
 
@@ -117,7 +117,7 @@ def setup_from(scan, z_ref=None, z_scene=None, compensate=True, Mx=None, My=None
     if z_scene is None or (isinstance(z_scene, float) and math.isnan(z_scene)):
         z_scene = g.z0 + 0.5 * (g.nz - 1) * g.dz
     return Setup(e, pos, tx, rx, float(scan.f0), float(scan.df), g.x0, g.y0, g.z0, g.dx, g.dy, g.dz,
-                 g.nx, g.ny, g.nz, float(z_ref), float(z_scene), bool(compensate),
+                 g.nx, g.ny, g.nz, float(z_ref), float(z_scene), int(compensate),
                  int(Mx or next_pow2(g.nx)), int(My or next_pow2(g.ny)))
 
 
@@ -149,14 +149,38 @@ def residual_beta(dxl, dyl, dzl, Zc):
     return -2.0 * dzl + (dxl * dxl + dyl * dyl) / (4.0 * Zc)
 
 
+def residual_beta_scene(xv, yv, dxl, dyl, dzl, x_s, y_s, Zc):
+    """Eq. 5 evaluated at a scatterer at the scene centre (x_s, y_s, z_ref + Z_c)
+    for a virtual element at (x', y', z_ref): the second-order round-trip
+    residual R^RT - 2 R_0 with the off-axis terms that Eq. 7 drops.  With +z
+    toward the scene, Z_0 - z of Eq. 5 is -Z_c:
+        R_0 = sqrt((x' - x_s)^2 + (y' - y_s)^2 + Z_c^2)
+        beta = -2 Z_c d^z / R_0 + (d^x^2 + d^y^2 + 4 d^z^2) / (4 R_0)
+               - [((x' - x_s) d^x + (y' - y_s) d^y)^2 + 4 Z_c^2 d^z^2] / (4 R_0^3)
+    On axis (x' = x_s, y' = y_s, R_0 = Z_c) it reduces to residual_beta."""
+    ax, ay = xv - x_s, yv - y_s
+    R0 = np.sqrt(ax * ax + ay * ay + Zc * Zc)
+    cross = ax * dxl + ay * dyl
+    return (-2.0 * Zc * dzl / R0 + (dxl * dxl + dyl * dyl + 4.0 * dzl * dzl) / (4.0 * R0)
+            - (cross * cross + 4.0 * Zc * Zc * dzl * dzl) / (4.0 * R0 ** 3))
+
+
 def compensate(su: Setup):
     """Eq. 11: s_hat(x', y', f) = s * exp(+j k beta_l).  Returns (s_hat [L, Nk],
-    x' [L], y' [L]) with the samples flattened in (t, r, p) order."""
+    x' [L], y' [L]) with the samples flattened in (t, r, p) order.  beta is
+    Eq. 12's residual (compensate = 1), or Eq. 5's at the scene centre
+    (compensate = 2); none for 0."""
     xv, yv, zl, dxl, dyl = virtual_elements(su.pos, su.tx, su.rx)
     L = xv.size
     s = su.echo.reshape(L, su.n_k).astype(np.complex128)
-    if su.compensate:
-        beta = residual_beta(dxl, dyl, zl - su.z_ref, su.z_scene - su.z_ref).ravel()
+    Zc = su.z_scene - su.z_ref
+    if su.compensate == 1:
+        beta = residual_beta(dxl, dyl, zl - su.z_ref, Zc).ravel()
+    elif su.compensate == 2:
+        beta = residual_beta_scene(xv, yv, dxl, dyl, zl - su.z_ref, su.x_c, su.y_c, Zc).ravel()
+    else:
+        beta = None
+    if beta is not None:
         s = s * np.exp(1j * np.outer(beta, su.wavenumbers))
     return s, xv.ravel(), yv.ravel()
 

@@ -47,7 +47,9 @@ def _ptr(t, what, dtype=None, numel=None):
 
 
 class Plan:
-    """Host-side plan for one acquisition shape and voxel grid."""
+    """Host-side plan for one acquisition shape and voxel grid.  ``compensate``:
+    1 (or True) applies Eq. 11-12 as the paper does, 2 uses the residual of
+    Eq. 5 evaluated at the scene centre, 0 (or False) skips compensation."""
 
     def __init__(self, n_tx, n_rx, n_pos, n_k, f0_hz, df_hz, grid, dtype="c64", z_ref=None, z_scene=None,
                  compensate=True, nufft_tol=1e-3, mx=0, my=0):
@@ -58,7 +60,7 @@ class Plan:
         g = grid
         self.grid = _lib.Grid(float(g.x0), float(g.y0), float(g.z0), float(g.dx), float(g.dy), float(g.dz),
                               int(g.nx), int(g.ny), int(g.nz))
-        self.opt = _lib.Options(_lib._nan(z_ref), _lib._nan(z_scene), int(bool(compensate)), float(nufft_tol),
+        self.opt = _lib.Options(_lib._nan(z_ref), _lib._nan(z_scene), int(compensate), float(nufft_tol),
                                 int(mx), int(my))
         self.dtype = dtype
         h = ctypes.c_void_p()

@@ -34,7 +34,8 @@ struct WsHeader {
     int zref_done;      // blocks of the z_ref reduction that have finished
     int pad_i;
     double inv_4zc;     // 1 / (4 Z_c), Z_c = z_scene - z_ref (0 without compensation)
-    double pad[8];
+    double zc;          // Z_c (0 without compensation)
+    double pad[7];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
 

@@ -105,7 +105,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     if (!(g.dx > 0) || !(g.dy > 0) || !(g.dz > 0) || !std::isfinite(g.x0) || !std::isfinite(g.y0) ||
         !std::isfinite(g.z0) || !std::isfinite(g.dx) || !std::isfinite(g.dy) || !std::isfinite(g.dz))
         return fail(MMSAR_ERR_INVALID_ARG, "grid pitches must be finite and > 0");
-    if (o.compensate != 0 && o.compensate != 1) return fail(MMSAR_ERR_INVALID_ARG, "compensate must be 0 or 1");
+    if (o.compensate < 0 || o.compensate > 2) return fail(MMSAR_ERR_INVALID_ARG, "compensate must be 0, 1 or 2");
     p.mx = o.mx > 0 ? o.mx : next_pow2(g.nx);
     p.my = o.my > 0 ? o.my : next_pow2(g.ny);
     if (p.mx < 16) p.mx = 16;

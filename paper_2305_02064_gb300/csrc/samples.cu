@@ -41,6 +41,7 @@ __device__ __forceinline__ void resolve_zref(double z_ref, double z_scene, int c
     const double Zc = z_scene - z_ref;
     if (compensate && !(Zc > 0.0)) atomicOr(&hdr->error, kErrGeometry);
     hdr->inv_4zc = (compensate && Zc > 0.0) ? 1.0 / (4.0 * Zc) : 0.0;
+    hdr->zc = (compensate && Zc > 0.0) ? Zc : 0.0;
 }
 
 __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__restrict__ pos, int P,
@@ -151,9 +152,23 @@ __device__ void geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int
         a.binid[l] = -1;
         return;
     }
-    // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
-    // (Z_c <= 0 was flagged once when z_ref was resolved; beta is then 0)
-    const double beta = (a.compensate && inv_4zc > 0.0) ? -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) * inv_4zc : 0.0;
+    // residual of the round trip over 2 R_0 (Z_c <= 0 was flagged once when
+    // z_ref was resolved; beta is then 0)
+    double beta = 0.0;
+    if (a.compensate == 1 && inv_4zc > 0.0) {
+        // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
+        beta = -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) * inv_4zc;
+    } else if (a.compensate == 2 && inv_4zc > 0.0) {
+        // Eq. 5 at the scene centre (x_c, y_c, z_ref + Z_c), Z_0 - z = -Z_c:
+        //   beta = -2 Z_c d^z / R_0 + (d^x^2 + d^y^2 + 4 d^z^2) / (4 R_0)
+        //          - [((x' - x_c) d^x + (y' - y_c) d^y)^2 + 4 Z_c^2 d^z^2] / (4 R_0^3)
+        const double Zc = a.hdr->zc, dz = zl - z_ref;
+        const double ax = xv - a.x_c, ay = yv - a.y_c;
+        const double R0 = sqrt(ax * ax + ay * ay + Zc * Zc);
+        const double cross = ax * ddx + ay * ddy;
+        beta = -2.0 * Zc * dz / R0 + (ddx * ddx + ddy * ddy + 4.0 * dz * dz) / (4.0 * R0) -
+               (cross * cross + 4.0 * Zc * Zc * dz * dz) / (4.0 * R0 * R0 * R0);
+    }
     // position on the 2M-point periodic grid, in cells
     const double gx = (xv - a.x_c) * a.inv_dx2;
     const double gy = (yv - a.y_c) * a.inv_dy2;

@@ -303,6 +303,27 @@ def large(seed: int = 5000, n_points: int = 2000) -> Scan:
     return Scan(s, pos, tx, rx, F0, BANDWIDTH / nk, grid, sc, "large", seed)
 
 
+def psf_track(dz_max: float, seed: int = 4000, n_pos: int = 256, nk: int = 64) -> Scan:
+    """The point-spread study of Sec. V-A: a linear MIMO array (2 Tx x 4 Rx
+    along y) moved along y over y' in [-12.5, 12.5] cm at x = 0 in n_pos
+    steps, on a semi-smooth random z track around the plane Z_0 = 0 whose
+    largest deviation |d^z| is dz_max; one unit point target at (0, 0, 0.5 m).
+    Image: the y-z plane x = 0, 256 x 64 voxels at 1 x 2.5 mm centred on the
+    target.  The single x column has a coarse x pitch (0.5 m), so the spectral
+    x grid collapses to k_x ~ 0 and the 3-D transform reduces to the 2-D (y, z)
+    one of a linear aperture (a finer x grid would add near-evanescent k_x
+    columns that the linear aperture does not resolve)."""
+    rng = np.random.default_rng(seed)
+    tx, rx = layout_awr1443()
+    pos = np.zeros((n_pos, 3))
+    pos[:, 1] = np.linspace(-0.125, 0.125, n_pos)
+    pos[:, 2] = _smooth_walk(n_pos, rng, dz_max)
+    grid = Grid(0.0, -0.128, 0.5 - 32 * 2.5e-3, 0.5, 1e-3, 2.5e-3, 1, 256, 64)
+    sc = np.array([[0.0, 0.0, 0.5, 1.0]])
+    s = echo(pos, tx, rx, F0, BANDWIDTH / nk, nk, sc)
+    return Scan(s, pos, tx, rx, F0, BANDWIDTH / nk, grid, sc, f"psf dz_max={dz_max:g}", seed)
+
+
 def custom(nx_pos=16, ny_pos=16, nk=32, layout="tiny", nx=32, ny=32, nz=16, dx=1e-3, dz=5e-3,
            z0=0.26, scatterers=None, n_points=3, jitter=(0.5e-3, 1e-3), serp=False,
            snr_db=None, seed=0, amplitude=False) -> Scan:

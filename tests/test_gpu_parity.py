@@ -78,7 +78,7 @@ def test_tiny_width8_matches_tighter(dev, tiny_scan):
     assert_parity(got, oracle_of(tiny_scan), 8)
 
 
-@pytest.mark.parametrize("compensate", [True, False])
+@pytest.mark.parametrize("compensate", [1, 0, 2])
 def test_ragged_sizes(dev, compensate):
     """Odd position counts, Nk not a multiple of 32, nx != ny, non-power-of-two
     nz: every tile, chunk and crop has a ragged edge."""
@@ -252,3 +252,31 @@ def test_single_plane_image(dev):
     got, plan = run_gpu(scan, dev, z_scene=0.30)
     assert got.shape == (32, 32, 1)
     assert_parity(got, oracle_of(scan, z_scene=0.30), plan.kernel_width)
+
+
+# ----------------------------------------------------------------------------- Sec. V-A PSF study
+@pytest.mark.parametrize("mode", [1, 2])
+def test_psf_track_parity(dev, mode):
+    """The linear-track point-target scan of the PSF study, samples up to
+    10 cm off the reference plane: GPU against the oracle for Eq. 7's and
+    Eq. 5's compensation."""
+    sc = synth.psf_track(0.10)
+    got, plan = run_gpu(sc, dev, z_ref=0.0, compensate=mode)
+    su = rma.setup_from(sc, z_ref=0.0, compensate=mode, Mx=plan.mx, My=plan.my)
+    assert_parity(got, rma.rma_fast(su, w=16), plan.kernel_width)
+
+
+def test_psf_study_ordering(dev):
+    """At 20 cm of plane deviation (more than 50 wavelengths), the GPU images
+    order as the study expects: Eq. 5 at the scene centre focuses best (peak
+    within a voxel of the target, narrowest cross-range lobe), Eq. 7 next,
+    no compensation last."""
+    from paper_2305_02064_gb300 import quality
+    sc = synth.psf_track(0.20)
+    m = {}
+    for mode in (0, 1, 2):
+        got, _ = run_gpu(sc, dev, z_ref=0.0, compensate=mode)
+        m[mode] = quality.psf_metrics(got, sc.grid, sc.scatterers[0])
+    assert m[2]["peak"] > m[1]["peak"] > m[0]["peak"]
+    assert m[2]["width_y_mm"] < m[1]["width_y_mm"]
+    assert abs(m[2]["peak_offset_y_mm"]) < 1.5 and abs(m[2]["peak_offset_z_mm"]) < 3.0   # within a voxel

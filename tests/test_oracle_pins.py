@@ -69,6 +69,35 @@ def test_beta_taylor_order(seed):
     assert res[2] < (1e-3) ** 3 / Zc ** 2
 
 
+@pytest.mark.parametrize("seed", range(5))
+def test_beta_scene_taylor_order_off_axis(seed):
+    """Eq. 5 at the scene centre for an off-axis virtual element: the exact
+    round trip minus 2 R_0 minus the refined residual vanishes as O(d^3),
+    while Eq. 7's on-axis residual is off at first order there (its -2 d^z
+    misses the Z_c / R_0 obliquity).  On axis the refined form equals Eq. 7's."""
+    rng = np.random.default_rng(100 + seed)
+    Zc, z_ref = 0.5, -0.02
+    xs, ys = 0.01, -0.02
+    xv, yv = xs + rng.uniform(0.05, 0.15), ys + rng.uniform(-0.12, 0.12)   # off axis
+    target = np.array([xs, ys, z_ref + Zc])
+    R0 = math.sqrt((xv - xs) ** 2 + (yv - ys) ** 2 + Zc ** 2)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    ref, eq7 = [], []
+    for eps in (2e-3, 1e-3, 5e-4):
+        d = eps * u
+        exact = _exact_round_trip(xv, yv, z_ref, d[0], d[1], d[2], target) - 2 * R0
+        ref.append(abs(exact - rma.residual_beta_scene(xv, yv, d[0], d[1], d[2], xs, ys, Zc)))
+        eq7.append(abs(exact - rma.residual_beta(d[0], d[1], d[2], Zc)))
+    assert 5.5 < ref[0] / ref[1] < 11 and 5.5 < ref[1] / ref[2] < 11, ref   # third order
+    assert eq7[0] / eq7[2] < 20, eq7     # at best second order (first order off axis)
+    assert all(r < 1e-2 * e for r, e in zip(ref, eq7)), (ref, eq7)
+    # on axis the two residuals coincide
+    d = 3e-3 * u
+    on = rma.residual_beta_scene(xs, ys, d[0], d[1], d[2], xs, ys, Zc)
+    assert on == pytest.approx(rma.residual_beta(d[0], d[1], d[2], Zc), rel=1e-12, abs=1e-15)
+
+
 def test_beta_sign_matters():
     """The opposite sign of the 2 d^z term leaves a residual ~ 4|d^z|."""
     Zc = 0.3
@@ -364,3 +393,50 @@ def test_peak_index_tie_break():
     assert rma.peak_index(v) == np.ravel_multi_index((0, 1, 2), v.shape)
     v[0, 1, 2] = 0.9
     assert rma.peak_index(v) == np.ravel_multi_index((1, 2, 3), v.shape)
+
+
+# ----------------------------------------------------------------------------- Sec. V-A PSF study
+def test_psf_study_compensation_modes():
+    """The point-spread study of Sec. V-A on the oracle: with the samples
+    spread +-5 cm off the reference plane, the uncompensated RMA loses the
+    target (peak far below the planar case, misplaced), Eq. 7's residual
+    recovers most of it, and Eq. 5 at the scene centre recovers the planar
+    PSF (same peak, position and main lobe); the planar case has the
+    closed-form cross-range width 0.886 lambda z / (2 D)."""
+    from paper_2305_02064_gb300 import quality
+    ref = None
+    for dz, mode in ((0.0, 1), (0.05, 0), (0.05, 1), (0.05, 2)):
+        sc = synth.psf_track(dz)
+        su = rma.setup_from(sc, z_ref=0.0, compensate=mode, Mx=16)
+        m = quality.psf_metrics(rma.rma_fast(su), sc.grid, sc.scatterers[0])
+        if ref is None:
+            ref = m
+            lam = synth.LAMBDA_C
+            assert m["width_y_mm"] == pytest.approx(0.886 * lam * 0.5 / (2 * 0.25) * 1e3, rel=0.05)
+            assert m["peak_offset_y_mm"] == 0 and m["peak_offset_z_mm"] == 0
+        elif mode == 0:
+            assert m["peak"] < 0.3 * ref["peak"]
+        elif mode == 1:
+            assert 0.6 * ref["peak"] < m["peak"] < 0.97 * ref["peak"]
+            assert m["width_y_mm"] > ref["width_y_mm"]
+        else:
+            assert m["peak"] == pytest.approx(ref["peak"], rel=0.01)
+            assert m["width_y_mm"] == pytest.approx(ref["width_y_mm"], rel=0.02)
+            assert abs(m["peak_offset_y_mm"]) < 1.5 and abs(m["peak_offset_z_mm"]) < 3
+
+
+def test_psf_metrics_gaussian():
+    """-3 dB widths of a separable Gaussian: 2 sigma sqrt(ln 2) per axis."""
+    from paper_2305_02064_gb300 import quality
+
+    class G:
+        x0, y0, z0, dx, dy, dz = 0.0, -0.128, 0.42, 1e-3, 1e-3, 2.5e-3
+
+    y = G.y0 + np.arange(256) * G.dy
+    z = G.z0 + np.arange(64) * G.dz
+    sy, sz = 3e-3, 10e-3
+    vol = np.exp(-0.5 * (y[None, :, None] / sy) ** 2 - 0.5 * ((z[None, None, :] - 0.5) / sz) ** 2) * np.ones((2, 1, 1))
+    m = quality.psf_metrics(vol, G, (0.0, 0.0, 0.5))
+    assert m["width_y_mm"] == pytest.approx(2 * sy * math.sqrt(math.log(2)) * 1e3, rel=0.02)
+    assert m["width_z_mm"] == pytest.approx(2 * sz * math.sqrt(math.log(2)) * 1e3, rel=0.02)
+    assert m["peak_offset_y_mm"] == 0 and m["peak_offset_z_mm"] == 0 and m["pslr_y_db"] == -np.inf
