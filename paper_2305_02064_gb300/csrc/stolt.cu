@@ -40,18 +40,28 @@ struct StoltArgs {
 
 constexpr int kStoltCols = 8;
 
-template <int MRZ, int WR>
+// complex elements of a warp's scratch region (even, so every region starts
+// on 16 bytes): the larger of 32 lane windows of WP points and the fallback's
+// staged samples (nk values + nk floats)
+__host__ __device__ inline int stolt_warp_scratch(int nk, int WP) {
+    const int a = 32 * WP, b = nk + (nk + 1) / 2;
+    const int m = a > b ? a : b;
+    return (m + 1) & ~1;
+}
+
+template <int MRZ, int WR, int GP>
 __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
     extern __shared__ float2 smem[];
-    constexpr int GP = fft_pitch(kStoltCols);            // padded row pitch of the grid tile
+    // GP: padded row pitch of the grid tile
     constexpr int WP = WR + 1;                            // padded pitch of a lane's window
     float2 *grid = smem;                                  // [MRZ][GP]
     float2 *tw = grid + MRZ * GP;                         // [MRZ]
-    float2 *winbuf = tw + MRZ;                            // [8 * 32][WP] per-lane register windows
-    float2 *cbuf = winbuf + kStoltCols * 32 * WP;         // [8][nk]
-    float *tbuf = reinterpret_cast<float *>(cbuf + kStoltCols * a.nk);  // [8][nk]
-    int *jlo_s = reinterpret_cast<int *>(tbuf + kStoltCols * a.nk);   // [8 * 32]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // per-warp scratch: either the lanes' register windows [32][WP] or, on the
+    // fallback path, the staged samples (values [nk], grid positions [nk])
+    const int wscr = stolt_warp_scratch(a.nk, WP);
+    float2 *scratch = tw + MRZ + warp * wscr;
+    int *jlo_s = reinterpret_cast<int *>(tw + MRZ + kStoltCols * wscr);   // [8 * 32]
     const int ncol = a.mx * a.my;
     __shared__ float turns_per_kz_s;   // (z_c - z_ref) / (2 pi): once per CTA (z_ref lives on the device)
     if (tid == 0) turns_per_kz_s = (float)((a.z_c - a.hdr->z_ref) * (0.5 / kPi));
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                         wr = fmul2(wr, make_float2(wr.y, qk));
                     }
                 }
-                float2 *mine = winbuf + (warp * 32 + lane) * WP;
+                float2 *mine = scratch + lane * WP;
 #pragma unroll
                 for (int i = 0; i < WR; ++i) mine[i] = acc[i];
                 jlo_s[warp * 32 + lane] = jl;
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                 // sum the windows per grid point, lanes in a fixed order
                 const int nact = (nv + per - 1) / per;
                 const int *jw = jlo_s + warp * 32;
-                const float2 *wb = winbuf + warp * 32 * WP;
+                const float2 *wb = scratch;
                 const int J_lo = jw[0], J_hi = jw[nact - 1] + WR - 1;
                 for (int jb = J_lo; jb <= J_hi; jb += 32) {
                     const int j = jb + lane;
@@ -167,8 +177,8 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                 // a run that spans more than the register window (very coarse
                 // depth sampling): stage the samples and gather each grid
                 // point from the samples in reach, found by binary search
-                float2 *cw = cbuf + warp * a.nk;
-                float *tw_ = tbuf + warp * a.nk;
+                float2 *cw = scratch;
+                float *tw_ = reinterpret_cast<float *>(scratch + a.nk);
                 for (int k = kf + lane; k < a.nk; k += 32) {
                     float t;
                     float2 c;
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
         }
     }
     __syncthreads();
-    smem_fft<MRZ, kStoltCols, 256, +1>(grid, tw);
+    smem_fft<MRZ, kStoltCols, 256, +1, GP>(grid, tw);
     if (col < ncol) {
         float2 *Zc = a.Z + (long long)col * a.nz;
         for (int q = lane; q < a.nz; q += 32) {
@@ -216,16 +226,20 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
     }
 }
 
-template <int MRZ, int WR>
-static cudaError_t launch_mrz_wr(const StoltArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)(MRZ * fft_pitch(kStoltCols) + MRZ + kStoltCols * 32 * (WR + 1)) * sizeof(float2) +
-                        (size_t)kStoltCols * a.nk * (sizeof(float2) + sizeof(float)) +
+template <int MRZ, int WR, int GP>
+static cudaError_t launch_mrz_wr_gp(const StoltArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)(MRZ * GP + MRZ + kStoltCols * stolt_warp_scratch(a.nk, WR + 1)) * sizeof(float2) +
                         (size_t)kStoltCols * 32 * sizeof(int);
-    cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR>, smem);
+    cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR, GP>, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.mx * a.my + kStoltCols - 1) / kStoltCols);
-    stolt_kernel<MRZ, WR><<<blocks, 256, smem, s>>>(a);
+    stolt_kernel<MRZ, WR, GP><<<blocks, 256, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int MRZ, int WR>
+static cudaError_t launch_mrz_wr(const StoltArgs &a, cudaStream_t s) {
+    return launch_mrz_wr_gp<MRZ, WR, fft_pitch(kStoltCols)>(a, s);
 }
 
 // register window: w + 2 grid points rounded up to an even count

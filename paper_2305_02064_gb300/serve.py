@@ -30,6 +30,7 @@ class ServeRequest:
     admitted: float = math.nan
     completed: float = math.nan
     result: object = None
+    pinned: object = None       # page-locked host copies of the inputs (GpuExecutor.pin)
 
     @property
     def latency(self) -> float:
@@ -107,7 +108,14 @@ def latency_summary(reqs):
 
 
 class GpuExecutor:
-    """CUDA executor: one stream per running request, pinned host echoes."""
+    """CUDA executor: one stream per running request, pinned host echoes.
+
+    Per request, on its stream: echo and geometry host -> device, FP16/BF16
+    quantisation with a per-scan scale (unless complex64), the image, and the
+    volume device -> host into a pinned buffer from a pool recycled by size;
+    the request is done when that copy has landed.  ``finish`` hands the
+    buffer back to the pool (keyed by volume shape) (``keep_results`` keeps a copy of the volume on
+    the request first, for checks outside timed runs)."""
 
     def __init__(self, device, dtype="f16", n_streams=8, keep_results=False):
         import torch
@@ -116,7 +124,7 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(n_streams)]
         self.free_streams = list(range(n_streams))
         self.keep = keep_results
-        self._pinned = {}
+        self._out_pool = collections.defaultdict(list)   # volume shape -> free pinned volumes
 
     def footprint(self, scan):
         from .batch import plan_for
@@ -131,9 +139,16 @@ class GpuExecutor:
         import numpy as np
         import torch
         s = req.scan
-        self._pinned[req.rid] = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                                 for a in (s.echo, np.asarray(s.pos, np.float64), np.asarray(s.tx, np.float64),
-                                           np.asarray(s.rx, np.float64))]
+        req.pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                      for a in (s.echo, np.asarray(s.pos, np.float64), np.asarray(s.tx, np.float64),
+                                np.asarray(s.rx, np.float64))]
+
+    def _out_buffer(self, shape):
+        import torch
+        free = self._out_pool[tuple(shape)]
+        if free:
+            return free.pop()
+        return torch.empty(shape, dtype=torch.complex64).pin_memory()
 
     def start(self, req):
         import torch
@@ -142,9 +157,10 @@ class GpuExecutor:
         si = self.free_streams.pop()
         st = self.streams[si]
         plan = plan_for(req.scan, dtype=self.dtype)
-        if req.rid not in self._pinned:
+        if req.pinned is None:
             self.pin(req)
-        echo_h, pos_h, tx_h, rx_h = self._pinned[req.rid]
+        echo_h, pos_h, tx_h, rx_h = req.pinned
+        vol_h = self._out_buffer(plan.volume_shape)
         with torch.cuda.stream(st):
             echo = echo_h.to(self.dev, non_blocking=True)
             pos, tx, rx = (t.to(self.dev, non_blocking=True) for t in (pos_h, tx_h, rx_h))
@@ -154,16 +170,20 @@ class GpuExecutor:
             ws = plan.new_workspace(self.dev)
             vol = plan.new_volume(self.dev)
             plan.image(ws, echo, pos, tx, rx, vol, echo_scale=scale, stream=st)
+            vol_h.copy_(vol, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        return {"req": req, "si": si, "ev": ev, "bufs": (echo, pos, tx, rx, ws, scale), "vol": vol, "plan": plan}
+        return {"req": req, "si": si, "ev": ev, "bufs": (echo, pos, tx, rx, ws, scale, vol), "vol_h": vol_h,
+                "plan": plan}
 
     def done(self, h):
         return h["ev"].query()
 
     def finish(self, h):
         h["plan"].poll_error(h["bufs"][4], stream=self.streams[h["si"]])
+        vol_h = h["vol_h"]
         if self.keep:
-            h["req"].result = h["vol"].cpu()
+            h["req"].result = vol_h.clone()
+        self._out_pool[tuple(vol_h.shape)].append(vol_h)
         self.free_streams.append(h["si"])
         h.clear()
