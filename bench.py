@@ -256,21 +256,27 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def csrc_digest():
+def csrc_digest(files=None):
+    """sha256 (first 16 hex digits) of the given source files (paths relative
+    to the repository root), or of every file under the package's csrc/."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2305_02064_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    if files is None:
+        files = sorted(os.path.relpath(p, ROOT) for p in glob.glob(os.path.join(ROOT, "paper_2305_02064_gb300",
+                                                                               "csrc", "*")))
+    for p in files:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(stage: str, workload: str):
-    """DRAM bytes per launch of the dominant stage from the committed ncu
-    summary, if it was taken on the current sources."""
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    summary, if it was taken on the current sources of that kernel (the
+    files listed with it) and on the same workload; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
         e = d["stages"][stage]
-        if d.get("csrc_sha") != csrc_digest() or d.get("workload") != workload:
+        if d.get("workload") != workload or e.get("sha") != csrc_digest(e["sources"]):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:

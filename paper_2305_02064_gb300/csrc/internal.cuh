@@ -32,7 +32,7 @@ struct WsHeader {
     // (mod the grid size) can be nonzero; everything else is known zero
     int u_lo, u_len, v_lo, v_len;
     int zref_done;      // blocks of the z_ref reduction that have finished
-    int pad_i;
+    int geom_done;      // blocks of the geometry pass that have finished
     double inv_4zc;     // 1 / (4 Z_c), Z_c = z_scene - z_ref (0 without compensation)
     double zc;          // Z_c (0 without compensation)
     double pad[7];
@@ -75,7 +75,7 @@ struct Plan {
 };
 
 constexpr int kStages = 8;
-constexpr int kKernelsPerImage = 11;
+constexpr int kKernelsPerImage = 10;
 
 }  // namespace mmsar
 
@@ -91,7 +91,6 @@ cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double
                         cudaStream_t s);
 cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
                             cudaStream_t s);
-cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);

@@ -278,7 +278,6 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_MARK(0);
     MMSAR_STEP(launch_zref(p, workspace, pos, tx, rx, s), "z_ref");
     MMSAR_STEP(launch_geometry(p, workspace, pos, tx, rx, s), "geometry");
-    MMSAR_STEP(launch_bin_scan(p, workspace, s), "bin scan");
     MMSAR_STEP(launch_bin_scatter(p, workspace, s), "bin scatter");
     MMSAR_MARK(1);
     MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation, bin sort and gridding weights");

@@ -34,7 +34,7 @@ namespace mmsar {
 // all samples (its reciprocal term 1 / (4 Z_c), and the check Z_c > 0).
 // Block 0 resets the occupied-window accumulators of the header.
 constexpr int kZrefThreads = 256;
-constexpr int kZrefMaxBlocks = 128;
+constexpr int kZrefMaxBlocks = 128;   // <= kZrefThreads (the last block loads one sum per thread)
 
 __device__ __forceinline__ void resolve_zref(double z_ref, double z_scene, int compensate, WsHeader *hdr) {
     hdr->z_ref = z_ref;
@@ -74,14 +74,21 @@ __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__rest
         last = atomicAdd(&hdr->zref_done, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
-    if (last && tid == 0) {
-        __threadfence();
-        double sum = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) sum += ((volatile double *)partials)[b];
+    if (!last) return;
+    // the last block: the block sums loaded in parallel (gridDim.x <= 256),
+    // then the same fixed-order tree as above
+    __threadfence();
+    red[tid] = tid < (int)gridDim.x ? ((volatile double *)partials)[tid] : 0.0;
+    __syncthreads();
+    for (int h = kZrefThreads / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] += red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
         double st = 0.0, sr = 0.0;
         for (int t = 0; t < T; ++t) st += tx[3 * t + 2];
         for (int r = 0; r < R; ++r) sr += rx[3 * r + 2];
-        resolve_zref((P > 0 ? sum / P : 0.0) + 0.5 * (st / T + sr / R), z_scene, compensate, hdr);
+        resolve_zref((P > 0 ? red[0] / P : 0.0) + 0.5 * (st / T + sr / R), z_scene, compensate, hdr);
     }
 }
 
@@ -108,17 +115,24 @@ struct GeomArgs {
     int compensate;
     double half_w;
     int mrx, mry, nbx;
-    double f0_over_c, df_over_c;
+    double f0_over_c32, df_over_c32;   // f0 / c and df / c times 2^32 (turns per metre, fixed point)
     WsHeader *hdr;
     int *counts;
+    int *offsets, *cursor;   // bin scan (last block)
+    int n_bins, w;
     int *binid;
     SampleRec *rec;
     uint2 *phase;
 };
 
-__device__ __forceinline__ uint32_t frac_to_fixed(double turns) {
-    const double f = turns - floor(turns);                       // [0, 1)
-    return (uint32_t)(unsigned long long)llrint(f * 4294967296.0);  // 2^32 wraps to 0
+// A phase given as turns x 2^32 -> 32-bit fixed-point turns: the low 32 bits
+// of the nearest integer are the phase modulo one turn (the scaling by 2^32
+// is exact, so this equals rounding frac(turns) 2^32).  Beyond 2^63 the
+// fraction is taken first.
+__device__ __forceinline__ uint32_t turns32_to_fixed(double t32) {
+    if (fabs(t32) < 9.0e18) return (uint32_t)(unsigned long long)llrint(t32);
+    const double f = t32 * 2.3283064365386963e-10;   // turns
+    return (uint32_t)(unsigned long long)llrint((f - floor(f)) * 4294967296.0);
 }
 
 __device__ __forceinline__ void box_reduce(int umin, int umax, int vmin, int vmax, WsHeader *hdr) {
@@ -136,7 +150,8 @@ __device__ __forceinline__ void box_reduce(int umin, int umax, int vmin, int vma
     }
 }
 
-__device__ void geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int &vmin, int &vmax) {
+// Returns the sample's bin (-1 when it is not binned); the caller counts it.
+__device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int &vmin, int &vmax) {
     const int tr = l / a.P, p = l - tr * a.P;
     const int t = tr / a.R, r = tr - t * a.R;
     const double px = a.pos[3 * p], py = a.pos[3 * p + 1], pz = a.pos[3 * p + 2];
@@ -150,7 +165,7 @@ __device__ void geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int
     if (!(isfinite(xv) && isfinite(yv) && isfinite(zl))) {
         atomicOr(&a.hdr->error, kErrNonfinite);
         a.binid[l] = -1;
-        return;
+        return -1;
     }
     // residual of the round trip over 2 R_0 (Z_c <= 0 was flagged once when
     // z_ref was resolved; beta is then 0)
@@ -193,19 +208,35 @@ __device__ void geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int
     rc.fy = (float)fy;
     a.rec[l] = rc;
     // Eq. 11 phase k beta = 2 pi f beta / c in turns: f0 beta/c + k df beta/c
-    a.phase[l] = make_uint2(frac_to_fixed(a.f0_over_c * beta), frac_to_fixed(a.df_over_c * beta));
+    a.phase[l] = make_uint2(turns32_to_fixed(a.f0_over_c32 * beta), turns32_to_fixed(a.df_over_c32 * beta));
     const int bin = (rc.v0 / kBin) * a.nbx + rc.u0 / kBin;
     a.binid[l] = bin;
-    atomicAdd(&a.counts[bin], 1);
+    return bin;
 }
 
+__device__ void scan_bins(const int *counts, int *__restrict__ offsets, int *__restrict__ cursor, int n,
+                          WsHeader *hdr, int w, int mrx, int mry, int *warp_tot);
+
 __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
+    __shared__ int warp_tot[32];
+    __shared__ bool last;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     int bumin = 0x7fffffff, bumax = -0x7fffffff - 1, bvmin = 0x7fffffff, bvmax = -0x7fffffff - 1;
-    if (l < a.L) {
-        geometry_one(a, l, bumin, bumax, bvmin, bvmax);
-    }
+    const int bin = l < a.L ? geometry_one(a, l, bumin, bumax, bvmin, bvmax) : -1;
+    // neighbouring samples share bins: one atomic per distinct bin of the warp
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.counts[bin], __popc(grp));
     box_reduce(bumin, bumax, bvmin, bvmax, a.hdr);
+    // the last block to finish turns the bin counts into offsets
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&a.hdr->geom_done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    scan_bins(a.counts, a.offsets, a.cursor, a.n_bins, a.hdr, a.w, a.mrx, a.mry, warp_tot);
 }
 
 cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
@@ -228,10 +259,14 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
     a.mrx = p.mrx;
     a.mry = p.mry;
     a.nbx = p.nbx;
-    a.f0_over_c = p.shape.f0_hz / kC0;
-    a.df_over_c = p.shape.df_hz / kC0;
+    a.f0_over_c32 = p.shape.f0_hz / kC0 * 4294967296.0;
+    a.df_over_c32 = p.shape.df_hz / kC0 * 4294967296.0;
     a.hdr = reinterpret_cast<WsHeader *>(w);
     a.counts = reinterpret_cast<int *>(w + p.off_counts);
+    a.offsets = reinterpret_cast<int *>(w + p.off_offsets);
+    a.cursor = reinterpret_cast<int *>(w + p.off_cursor);
+    a.n_bins = (int)p.n_bins;
+    a.w = p.w;
     a.binid = reinterpret_cast<int *>(w + p.off_binid);
     a.rec = reinterpret_cast<SampleRec *>(w + p.off_rec);
     a.phase = reinterpret_cast<uint2 *>(w + p.off_phase);
@@ -261,17 +296,18 @@ __device__ __forceinline__ void finish_window(int vmin, int vmax, int w, int m, 
     *len = (int)span;
 }
 
-// Exclusive prefix sum of the bin counts in one block, in rounds of
-// kScanThreads x kScanPer bins: thread t loads its kScanPer consecutive bins
-// with 16-byte loads, the block scans the per-thread sums with warp shuffles,
-// and every thread writes its bins' offsets (also the scatter cursors); the
-// running total carries to the next round.  The bin count is a multiple of 4.
-// Thread 0 finalises the occupied window and the binned-sample count.
-constexpr int kScanThreads = 1024;
+// Exclusive prefix sum of the bin counts by one block (the last block of the
+// geometry pass), in rounds of blockDim.x x kScanPer bins: thread t loads its
+// kScanPer consecutive bins with 16-byte loads from L2 (the counts were
+// built by atomics of other blocks), the block scans the per-thread sums with
+// warp shuffles, and every thread writes its bins' offsets (also the scatter
+// cursors); the running total carries to the next round.  The bin count is
+// a multiple of 4.  Thread 0 finalises the occupied window and the
+// binned-sample count.
 constexpr int kScanPer = 16;
 
-__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int x = v;
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -280,7 +316,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
     if (lane == 31) warp_tot[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int t = warp_tot[lane];
+        int t = lane < nw ? warp_tot[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += y;
@@ -288,24 +324,24 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot) {
         warp_tot[lane] = t;   // inclusive over warps
     }
     __syncthreads();
+    total = warp_tot[nw - 1];
     return x - v + (warp > 0 ? warp_tot[warp - 1] : 0);
 }
 
-__global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const int *__restrict__ counts,
-                                                                int *__restrict__ offsets, int *__restrict__ cursor,
-                                                                int n, WsHeader *hdr, int w, int mrx, int mry) {
-    __shared__ int warp_tot[32];
+__device__ void scan_bins(const int *counts, int *__restrict__ offsets, int *__restrict__ cursor, int n,
+                          WsHeader *hdr, int w, int mrx, int mry, int *warp_tot) {
     int carry = 0;
-    for (int base = 0; base < n; base += kScanThreads * kScanPer) {
+    for (int base = 0; base < n; base += blockDim.x * kScanPer) {
         const int b0 = base + threadIdx.x * kScanPer;
         int4 c[kScanPer / 4];
         int sum = 0;
 #pragma unroll
         for (int q = 0; q < kScanPer / 4; ++q) {
-            c[q] = b0 + 4 * q < n ? *reinterpret_cast<const int4 *>(counts + b0 + 4 * q) : make_int4(0, 0, 0, 0);
+            c[q] = b0 + 4 * q < n ? __ldcg(reinterpret_cast<const int4 *>(counts + b0 + 4 * q)) : make_int4(0, 0, 0, 0);
             sum += c[q].x + c[q].y + c[q].z + c[q].w;
         }
-        int run = carry + block_exclusive_scan(sum, warp_tot);
+        int total;
+        int run = carry + block_exclusive_scan(sum, warp_tot, total);
 #pragma unroll
         for (int q = 0; q < kScanPer / 4; ++q) {
             if (b0 + 4 * q >= n) break;
@@ -318,36 +354,33 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const int *__res
             *reinterpret_cast<int4 *>(offsets + b0 + 4 * q) = o;
             *reinterpret_cast<int4 *>(cursor + b0 + 4 * q) = o;
         }
-        carry += warp_tot[31];
+        carry += total;
         __syncthreads();   // warp_tot is reused by the next round
     }
     if (threadIdx.x == 0) {
         offsets[n] = carry;
         hdr->n_valid = carry;
-        finish_window(hdr->u_min, hdr->u_max, w, mrx, &hdr->u_lo, &hdr->u_len);
-        finish_window(hdr->v_min, hdr->v_max, w, mry, &hdr->v_lo, &hdr->v_len);
+        volatile WsHeader *vh = hdr;
+        finish_window(vh->u_min, vh->u_max, w, mrx, &hdr->u_lo, &hdr->u_len);
+        finish_window(vh->v_min, vh->v_max, w, mry, &hdr->v_lo, &hdr->v_len);
     }
 }
 
-cudaError_t launch_bin_scan(const Plan &p, void *ws, cudaStream_t s) {
-    char *w = reinterpret_cast<char *>(ws);
-    bin_scan_kernel<<<1, kScanThreads, 0, s>>>(reinterpret_cast<int *>(w + p.off_counts),
-                                               reinterpret_cast<int *>(w + p.off_offsets),
-                                               reinterpret_cast<int *>(w + p.off_cursor), (int)p.n_bins,
-                                               reinterpret_cast<WsHeader *>(w), p.w, p.mrx, p.mry);
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ bin scatter
-// Each sample takes the next slot of its bin (arrival order of the atomics;
-// the in-bin order is made deterministic afterwards, see spread.cu).
+// Each sample takes a slot of its bin: the lanes of a warp that share a bin
+// reserve their slots with one atomic and take them in lane order (the
+// in-bin order is made deterministic afterwards by the in-bin sort).
 __global__ void __launch_bounds__(256) bin_scatter_kernel(int L, const int *__restrict__ binid,
                                                           int *__restrict__ cursor, int *__restrict__ perm) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= L) return;
-    const int b = binid[l];
-    if (b < 0) return;
-    perm[atomicAdd(&cursor[b], 1)] = l;
+    const int lane = threadIdx.x & 31;
+    const int b = l < L ? binid[l] : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (b >= 0 && lane == leader) base = atomicAdd(&cursor[b], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b >= 0) perm[base + __popc(grp & ((1u << lane) - 1u))] = l;
 }
 
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
