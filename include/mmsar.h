@@ -114,6 +114,21 @@ mmsar_status mmsar_plan_workspace_bytes(const mmsar_plan *plan, size_t *bytes);
 mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx, int *my,
                              int *kernels_per_image);
 
+/* Launch shape of the gridding stage (the spreading step of Sec. III's
+ * Gaussian gridding).  Every shape computes the same image, bit for bit
+ * within one shape; they differ only in speed, which depends on the scan's
+ * size (small scans fill the GPU better with smaller CTAs).  Defaults: 2, 8. */
+typedef struct {
+    int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64           */
+    int grid_warps_per_cta;    /* 4: an 8 x 8-cell tile; 8: a 16 x 8-cell tile     */
+} mmsar_tiles;
+
+/* Set (or read) the plan's gridding launch shape; the autotuner of the
+ * Python package times the shapes on the caller's data and sets the
+ * fastest.  INVALID_ARG for other values.  Not thread-safe (like the plan). */
+mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles);
+mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles);
+
 /* Stages of mmsar_image, in launch order: 0 "prep" (reference plane,
  * geometry of Eq. 3-4 and 12, binning), 1 "compensate" (Eq. 11),
  * 2 "grid" (Gaussian gridding), 3 "fft_x", 4 "fft_y" (FT_2D of Eq. 16 with

@@ -75,6 +75,7 @@ class Plan:
         self.kernel_width, self.mx, self.my = w.value, mxv.value, myv.value
         self.kernels_per_image = kpi.value
         self._events = None
+        self.tuned = None       # set by tune.autotune
 
     @classmethod
     def for_scan(cls, scan, **kw):
@@ -87,6 +88,17 @@ class Plan:
         if h is not None and h.value:
             self._lib.mmsar_plan_destroy(h)
             self._h = None
+
+    def set_tiles(self, freqs_per_lane: int, warps_per_cta: int):
+        """Gridding launch shape (see mmsar_plan_set_tiles; tune.autotune picks one)."""
+        _lib.check(self._lib.mmsar_plan_set_tiles(self._h, ctypes.byref(_lib.Tiles(int(freqs_per_lane),
+                                                                                 int(warps_per_cta)))))
+
+    @property
+    def tiles(self):
+        t = _lib.Tiles()
+        _lib.check(self._lib.mmsar_plan_get_tiles(self._h, ctypes.byref(t)))
+        return (t.grid_freqs_per_lane, t.grid_warps_per_cta)
 
     @property
     def volume_shape(self):

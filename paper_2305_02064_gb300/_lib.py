@@ -27,7 +27,8 @@ EXPORTS = ["mmsar_options_default", "mmsar_plan_create", "mmsar_plan_workspace_b
            "mmsar_stage_count", "mmsar_stage_name", "mmsar_plan_set_stage_events",
            "mmsar_image", "mmsar_poll_error", "mmsar_peak_scratch_bytes", "mmsar_peak", "mmsar_last_error",
            "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static",
-           "mmsar_quantize_echo", "mmsar_image_batch", "mmsar_backproject"]
+           "mmsar_quantize_echo", "mmsar_image_batch", "mmsar_backproject", "mmsar_plan_set_tiles",
+           "mmsar_plan_get_tiles"]
 
 
 class MmsarError(RuntimeError):
@@ -51,6 +52,10 @@ class Grid(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class Tiles(ctypes.Structure):
+    _fields_ = [("grid_freqs_per_lane", ctypes.c_int), ("grid_warps_per_cta", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):
@@ -113,6 +118,10 @@ def load(build_if_missing: bool = True):
         lib.mmsar_image_batch.restype = ctypes.c_int
         lib.mmsar_backproject.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp]
         lib.mmsar_backproject.restype = ctypes.c_int
+        lib.mmsar_plan_set_tiles.argtypes = [vp, ctypes.POINTER(Tiles)]
+        lib.mmsar_plan_set_tiles.restype = ctypes.c_int
+        lib.mmsar_plan_get_tiles.argtypes = [vp, ctypes.POINTER(Tiles)]
+        lib.mmsar_plan_get_tiles.restype = ctypes.c_int
         lib.mmsar_version.argtypes = []
         lib.mmsar_version.restype = ctypes.c_char_p
         _LIB = lib

@@ -63,6 +63,15 @@ class ScanJob:
                             self.scale.data_ptr() if self.scale is not None else None, self.pos.data_ptr(),
                             self.tx.data_ptr(), self.rx.data_ptr(), self.vol.data_ptr())
 
+    def tune(self, stream=None):
+        """Autotune the gridding launch shape of this job's plan on its own data
+        (once per plan: jobs of one shape share it)."""
+        from .tune import autotune
+        if self.plan.tuned is None:
+            autotune(self.plan, self.ws, self.echo, self.pos, self.tx, self.rx, self.vol, echo_scale=self.scale,
+                     stream=stream)
+        return self.plan.tuned
+
     def image(self, stream=None):
         self.plan.image(self.ws, self.echo, self.pos, self.tx, self.rx, self.vol, echo_scale=self.scale,
                         stream=stream)

@@ -58,6 +58,8 @@ struct Plan {
     int nkp;            // n_kc * 32
     int64_t L;          // n_tx n_rx n_pos
     int nbx, nby;       // bins per axis (mrx / 4, mry / 4)
+    int spread_nf;      // gridding launch shape: frequencies per lane (1 or 2)
+    int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells)
     int64_t n_bins;
     bool zref_given;
     double z_ref;       // when given

@@ -129,6 +129,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.nbx = p.mrx / kBin;
     p.nby = p.mry / kBin;
     p.n_bins = (int64_t)p.nbx * p.nby;
+    p.spread_nf = 2;
+    p.spread_warps = 8;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;
     p.z_scene = std::isfinite(o.z_scene) ? o.z_scene : g.z0 + 0.5 * (g.nz - 1) * g.dz;
@@ -223,6 +225,24 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
     if (mx) *mx = plan->p.mx;
     if (my) *my = plan->p.my;
     if (kernels_per_image) *kernels_per_image = plan->p.L > 0 ? kKernelsPerImage : 0;
+    return MMSAR_OK;
+}
+
+mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
+    if (!plan || !tiles) return fail(MMSAR_ERR_INVALID_ARG, "null plan or tiles");
+    if (tiles->grid_freqs_per_lane != 1 && tiles->grid_freqs_per_lane != 2)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_freqs_per_lane must be 1 or 2");
+    if (tiles->grid_warps_per_cta != 4 && tiles->grid_warps_per_cta != 8)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_warps_per_cta must be 4 or 8");
+    plan->p.spread_nf = tiles->grid_freqs_per_lane;
+    plan->p.spread_warps = tiles->grid_warps_per_cta;
+    return MMSAR_OK;
+}
+
+mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles) {
+    if (!plan || !tiles) return fail(MMSAR_ERR_INVALID_ARG, "null plan or tiles");
+    tiles->grid_freqs_per_lane = plan->p.spread_nf;
+    tiles->grid_warps_per_cta = plan->p.spread_warps;
     return MMSAR_OK;
 }
 

@@ -54,44 +54,49 @@ __device__ __forceinline__ bool tile_meets(int t0, int span, int lo, int len, in
     return d < len || e < span;
 }
 
-constexpr int kSpreadThreads = 256;   // 8 warps: a 16 x 8-cell tile
+constexpr int kListCap = 192;   // relevant samples listed per warp before they are applied
 
-constexpr int kListCap = 192;
-constexpr int kSpreadChunks = 2;   // frequency chunks of 32 per CTA   // relevant samples listed per warp before they are applied
-
-template <int NS, int MINB>
-__global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs a) {
+// NF: frequencies per lane (1: a CTA covers one chunk of 32 frequencies; 2:
+// a 64-frequency group, lane l holding frequencies 2l and 2l + 1); WARPS: 8
+// (a 16 x 8-cell tile) or 4 (8 x 8 cells), each warp a 4 x 4-cell block.
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spread_kernel(SpreadArgs a) {
+    constexpr int TX = 4 * (WARPS / 2);   // tile width in cells (two block rows)
     // per warp: (x-quad index, y-quad index, sample index) of each listed sample
-    __shared__ int4 lists[kSpreadThreads / 32][kListCap];
+    __shared__ int4 lists[WARPS][kListCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tiles_x = a.mrx >> 4;
-    // a CTA covers one 64-frequency group (two chunks of 32); lane l holds
-    // frequencies 2l and 2l + 1 of the group.  The group varies fastest, so
-    // the groups of one tile run together and share its weight records in L2
-    const int n_kg = (a.n_kc + 1) / 2;
+    const int tiles_x = a.mrx / TX;
+    // the frequency group varies fastest, so the groups of one tile run
+    // together and share its weight records in L2
+    const int n_kg = NF == 2 ? (a.n_kc + 1) / 2 : a.n_kc;
     const int kg = blockIdx.x % n_kg;
     const int tile = blockIdx.x / n_kg;
     // tiles outside the occupied window stay unwritten: the FFT along x'
     // reads only the window and takes the rest as zero
-    if (!tile_meets((tile % tiles_x) * 16, 16, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
+    if (!tile_meets((tile % tiles_x) * TX, TX, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
         !tile_meets((tile / tiles_x) * 8, 8, a.hdr->v_lo, a.hdr->v_len, a.mry))
         return;
-    const int U = (tile % tiles_x) * 16 + (warp & 3) * 4;
-    const int V = (tile / tiles_x) * 8 + (warp >> 2) * 4;
+    const int U = (tile % tiles_x) * TX + (warp % (WARPS / 2)) * 4;
+    const int V = (tile / tiles_x) * 8 + (warp / (WARPS / 2)) * 4;
     const int rq = 2 * (a.w + 3) + 1;
     const int nq = a.w + 3;
-    float4 acc[4][4];   // (re, im) of frequency 2l, then of 2l + 1
+    float2 acc[NF][4][4];   // (re, im) per frequency of the lane and cell
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[j][i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // s_hat group kg: [Lmax][64] complex, 16 bytes per lane per sample
-    const float4 *sh = reinterpret_cast<const float4 *>(a.shat) + (long long)kg * a.Lmax * 32 + lane;
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[f][j][i] = make_float2(0.f, 0.f);
+    // s_hat: [n_kc / 2][Lmax][64] complex; the lane's NF values of a sample
+    // are 8 NF contiguous bytes at row offset (sample * 64 + col0) complex
+    const int col0 = NF == 2 ? 2 * lane : (kg & 1) * 32 + lane;
+    const float2 *sh = a.shat + (long long)(NF == 2 ? kg : kg >> 1) * a.Lmax * 64 + col0;
     int4 *list = lists[warp];
 
     // one listed sample in flight: its x and y weight quads and its values
     struct Stage {
-        float4 x, y, v;
+        float4 x, y;
+        float2 v[NF];
     };
     // apply the listed samples through an NS-deep pipeline: the loads of
     // entry i + NS are issued as soon as entry i has been accumulated
@@ -101,23 +106,27 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
             const int4 e = list[i];
             q.x = __ldg(a.wrec + e.x);
             q.y = __ldg(a.wrec + e.y);
-            q.v = __ldg(sh + (e.z << 5));
+            if constexpr (NF == 2) {
+                // sample index * 32 < 2^31 (plan limit): 32-bit offsets in float4 units
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(sh) + (e.z << 5));
+                q.v[0] = make_float2(t.x, t.y);
+                q.v[NF - 1] = make_float2(t.z, t.w);
+            } else {
+                q.v[0] = __ldg(sh + ((long long)e.z << 6));
+            }
         };
         auto consume = [&](const Stage &q) {
             const float wx[4] = {q.x.x, q.x.y, q.x.z, q.x.w};
             const float wy[4] = {q.y.x, q.y.y, q.y.z, q.y.w};
-            const float2 v0 = make_float2(q.v.x, q.v.y), v1 = make_float2(q.v.z, q.v.w);
             // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float2 wyj = make_float2(wy[j], wy[j]);
-                const float2 t0 = fmul2(wyj, v0), t1 = fmul2(wyj, v1);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 wxi = make_float2(wx[i], wx[i]);
-                    const float2 a0 = ffma2(wxi, t0, make_float2(acc[j][i].x, acc[j][i].y));
-                    const float2 a1 = ffma2(wxi, t1, make_float2(acc[j][i].z, acc[j][i].w));
-                    acc[j][i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                for (int f = 0; f < NF; ++f) {
+                    const float2 t = fmul2(wyj, q.v[f]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[f][j][i] = ffma2(make_float2(wx[i], wx[i]), t, acc[f][j][i]);
                 }
             }
         };
@@ -173,15 +182,25 @@ __global__ void __launch_bounds__(kSpreadThreads, MINB) spread_kernel(SpreadArgs
     }
     __syncwarp();
     apply(n);
-    // lanes 0..15 hold chunk 2 kg, lanes 16..31 chunk 2 kg + 1 (absent when
-    // the chunk count is odd): 16 bytes per lane, 256 contiguous bytes per chunk
-    const int kc = 2 * kg + (lane >> 4);
-    if (kc < a.n_kc) {
-        float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + (lane & 15);
+    if constexpr (NF == 2) {
+        // lanes 0..15 hold chunk 2 kg, lanes 16..31 chunk 2 kg + 1 (absent when
+        // the chunk count is odd): 16 bytes per lane, 256 contiguous bytes per chunk
+        const int kc = 2 * kg + (lane >> 4);
+        if (kc < a.n_kc) {
+            float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + (lane & 15);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    g[((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2)] =
+                        make_float4(acc[0][j][i].x, acc[0][j][i].y, acc[NF - 1][j][i].x, acc[NF - 1][j][i].y);
+        }
+    } else {
+        float2 *g = a.G + (long long)kg * a.mry * a.mrx * kKC + lane;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2)] = acc[j][i];
+            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC] = acc[0][j][i];
     }
 }
 
@@ -202,10 +221,20 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
-    // a 64-frequency group per CTA (a lane holds two frequencies), three
-    // listed samples in flight, two CTAs per SM
-    const unsigned tiles = (unsigned)((p.mrx / 16) * (p.mry / 8));
-    spread_kernel<3, 2><<<tiles * ((p.n_kc + 1) / 2), kSpreadThreads, 0, s>>>(a);
+    // the launch shape is the plan's (set by mmsar_plan_set_tiles, e.g. from
+    // the autotuner): NF frequencies per lane, WARPS warps per CTA; three
+    // listed samples in flight
+    const int nf = p.spread_nf, warps = p.spread_warps;
+    const unsigned tiles = (unsigned)((p.mrx / (2 * warps)) * (p.mry / 8));
+    const unsigned blocks = tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
+    if (nf == 2 && warps == 8)
+        spread_kernel<2, 8, 3, 2><<<blocks, 256, 0, s>>>(a);
+    else if (nf == 2)
+        spread_kernel<2, 4, 3, 4><<<blocks, 128, 0, s>>>(a);
+    else if (warps == 8)
+        spread_kernel<1, 8, 3, 3><<<blocks, 256, 0, s>>>(a);
+    else
+        spread_kernel<1, 4, 3, 6><<<blocks, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

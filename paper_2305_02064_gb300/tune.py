@@ -1,0 +1,37 @@
+"""Autotuner of the gridding launch shape.
+
+Every shape of ``mmsar_tiles`` computes the same image; which is fastest
+depends on the scan (a small scan fills the GPU better with CTAs over 32
+frequencies or 8 x 8-cell tiles, a large one prefers 64 frequencies and
+16 x 8 cells).  ``autotune`` images the caller's own data with each shape on
+the caller's stream, timed with CUDA events, and leaves the plan set to the
+fastest; the result is kept on the plan, so plans shared by scans of one
+shape are tuned once.  Only the plan's launch shape changes: the kernels
+and the images are the library's.
+"""
+from __future__ import annotations
+
+SHAPES = ((2, 8), (1, 8), (2, 4), (1, 4))   # (frequencies per lane, warps per CTA)
+
+
+def autotune(plan, ws, echo, pos, tx, rx, vol, echo_scale=None, stream=None, reps: int = 3,
+             shapes=SHAPES) -> dict:
+    """Time ``reps`` images per launch shape (after one untimed image) and set
+    the fastest on ``plan``.  Returns {"tiles": (nf, warps), "ms": {shape: ms}}."""
+    import torch
+    st = stream or torch.cuda.current_stream(vol.device)
+    times = {}
+    for shp in shapes:
+        plan.set_tiles(*shp)
+        plan.image(ws, echo, pos, tx, rx, vol, echo_scale=echo_scale, stream=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            plan.image(ws, echo, pos, tx, rx, vol, echo_scale=echo_scale, stream=st)
+        e1.record(st)
+        e1.synchronize()
+        times[shp] = e0.elapsed_time(e1) / reps
+    best = min(times, key=times.get)
+    plan.set_tiles(*best)
+    plan.tuned = {"tiles": best, "ms": times}
+    return plan.tuned

@@ -96,3 +96,18 @@ def test_realistic_workspace_fits_hbm():
     s = synth.Grid(-0.128, -0.128, 0.2, 1e-3, 1e-3, 3.125e-3, 256, 256, 64)
     p = Plan(2, 4, 16384, 256, 77e9, 4e9 / 256, s)
     assert p.workspace_bytes < 2 * 1024 ** 3
+
+
+def test_gridding_launch_shape_setter():
+    """mmsar_plan_set_tiles accepts the four gridding launch shapes and
+    rejects everything else; the default is 64 frequencies on 8 warps."""
+    from paper_2305_02064_gb300._lib import MmsarError
+    p = _plan()
+    assert p.tiles == (2, 8)
+    for shp in ((1, 4), (2, 4), (1, 8), (2, 8)):
+        p.set_tiles(*shp)
+        assert p.tiles == shp
+    for bad in ((0, 8), (3, 8), (2, 2), (2, 16), (-1, 4)):
+        with pytest.raises(MmsarError, match="INVALID_ARG"):
+            p.set_tiles(*bad)
+    assert p.tiles == (2, 8)

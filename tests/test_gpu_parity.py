@@ -280,3 +280,39 @@ def test_psf_study_ordering(dev):
     assert m[2]["peak"] > m[1]["peak"] > m[0]["peak"]
     assert m[2]["width_y_mm"] < m[1]["width_y_mm"]
     assert abs(m[2]["peak_offset_y_mm"]) < 1.5 and abs(m[2]["peak_offset_z_mm"]) < 3.0   # within a voxel
+
+
+# ----------------------------------------------------------------------------- gridding launch shapes
+def test_gridding_launch_shapes_are_bit_identical(dev):
+    """Every gridding launch shape visits the samples of a cell in the same
+    order with the same arithmetic: the volumes are bit-identical, and they
+    match the oracle."""
+    scan = synth.custom(nx_pos=9, ny_pos=7, nk=40, layout="awr1443", nx=24, ny=20, nz=10, seed=21,
+                        jitter=(0.7e-3, 3e-3), snr_db=25)
+    from paper_2305_02064_gb300 import Plan
+    vols = {}
+    for shp in ((2, 8), (1, 8), (2, 4), (1, 4)):
+        plan = Plan.for_scan(scan)
+        plan.set_tiles(*shp)
+        ws = plan.new_workspace(dev)
+        vol = torch.full(plan.volume_shape, complex(np.nan, np.nan), dtype=torch.complex64, device=dev)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        plan.image(ws, t(scan.echo), t(np.asarray(scan.pos, np.float64)), t(np.asarray(scan.tx, np.float64)),
+                   t(np.asarray(scan.rx, np.float64)), vol)
+        plan.poll_error(ws)
+        vols[shp] = vol.cpu().numpy()
+    ref = vols[(2, 8)]
+    for shp, v in vols.items():
+        assert np.array_equal(v.view(np.uint64), ref.view(np.uint64)), shp
+    assert_parity(ref, oracle_of(scan), 6)
+
+
+def test_autotune_picks_a_shape_and_keeps_the_image(dev, tiny_scan):
+    from paper_2305_02064_gb300.batch import ScanJob
+    from paper_2305_02064_gb300.tune import SHAPES
+    job = ScanJob(tiny_scan, dev)
+    res = job.tune()
+    assert res["tiles"] in SHAPES and job.plan.tiles == res["tiles"] and len(res["ms"]) == len(SHAPES)
+    job.image()
+    torch.cuda.synchronize()
+    assert_parity(job.vol.cpu().numpy(), oracle_of(tiny_scan), 6)
