@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=256, help="requests in the serving run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default gridding launch shape")
     return ap.parse_args()
 
 
@@ -303,6 +304,12 @@ def run_ours(args, dist):
     echo, pos, tx, rx = (t.to(dev) for t in (echo_h, pos_h, tx_h, rx_h))
     vol_h = torch.empty(vol.shape, dtype=vol.dtype).pin_memory()
     torch.cuda.synchronize(dev)
+    # the autotuner picks the gridding launch shape on this scan (untimed)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2305_02064_gb300.tune import autotune
+        tuned = autotune(plan, ws, echo, pos, tx, rx, vol, stream=stream)
+        torch.cuda.synchronize(dev)
 
     def step():
         plan.image(ws, echo, pos, tx, rx, vol, stream=stream)
@@ -429,6 +436,9 @@ def run_ours(args, dist):
                 "serial_ms_per_step": e2e_serial_ms, "serial_value": total_vox / (e2e_serial_ms * 1e-3)},
         "gpu_launches": plan.kernels_per_image * args.steps,
         "clocks": clk,
+        "grid_launch_shape": {"freqs_per_lane": plan.tiles[0], "warps_per_cta": plan.tiles[1],
+                              "autotuned_ms": None if tuned is None else
+                              {f"{a}x{b}": round(v, 4) for (a, b), v in tuned["ms"].items()}},
     }
     return res, scan, vol
 

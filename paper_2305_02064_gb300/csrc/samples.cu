@@ -460,10 +460,9 @@ __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *
 
 // -- compensation (Eq. 11)
 // One warp per group of kCompUnroll samples and one 64-frequency group g:
-// lane l reads s[l][64 g + l] and s[l][64 g + 32 + l] for each sample of the
-// group (the loads of the group are issued together, 256 coalesced bytes
-// each), rotates them by exp(+j 2 pi (a + k b)) and writes s_hat in original
-// sample order with the two halves of the group side by side,
+// each lane reads two frequencies of each sample of the group (the loads of
+// the group are issued together and coalesced), rotates them by
+// exp(+j 2 pi (a + k b)) and writes s_hat in original sample order,
 // s_hat[g][l][0..63] (512 contiguous bytes per sample; frequencies past Nk
 // are written as zero).
 constexpr int kCompUnroll = 4;
@@ -481,6 +480,40 @@ __device__ __forceinline__ float2 load_echo(const void *__restrict__ echo_v, lon
         float2 v = __bfloat1622float2(h);
         return make_float2(v.x * scale, v.y * scale);
     }
+}
+
+// Two adjacent complex samples (pair index e2 = element index / 2): 16 bytes
+// of complex64 or 8 bytes of scaled FP16 / BF16 pairs.
+template <int DT>
+__device__ __forceinline__ void load_echo2(const void *__restrict__ echo_v, long long e2, float scale, float2 &v0,
+                                           float2 &v1) {
+    if (DT == MMSAR_ECHO_C64) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(echo_v) + e2);
+        v0 = make_float2(t.x, t.y);
+        v1 = make_float2(t.z, t.w);
+    } else {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(echo_v) + e2);
+        float2 a, b;
+        if (DT == MMSAR_ECHO_F16X2_SCALED) {
+            a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+            b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        } else {
+            a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+            b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+        }
+        v0 = make_float2(a.x * scale, a.y * scale);
+        v1 = make_float2(b.x * scale, b.y * scale);
+    }
+}
+
+// exp(+j 2 pi turns / 2^32) applied to v; the angle is already reduced to
+// [-pi, pi), where the hardware sine and cosine (absolute error ~4e-7) are
+// accurate enough
+__device__ __forceinline__ float2 rotate_turns(float2 v, uint32_t turns) {
+    const float ang = (float)(int32_t)turns * 1.4629180792671596e-09f;   // 2 pi turns / 2^32
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    return cmul(v, make_float2(cs, sn));
 }
 
 struct PrepTailArgs {
@@ -502,7 +535,10 @@ struct PrepTailArgs {
     float2 *shat;
 };
 
-template <int DT>
+// VEC: lane l takes the adjacent frequencies 64 g + 2 l and 64 g + 2 l + 1
+// (one 16-byte or 8-byte load, one 16-byte store per sample; Nk even and the
+// echo aligned); otherwise 64 g + l and 64 g + 32 + l.
+template <int DT, bool VEC>
 __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArgs a) {
     __shared__ int keys[kPrepWarps][kSortBinCap];
     __shared__ int sorted[kPrepWarps][kSortBinCap];
@@ -526,33 +562,45 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
         for (int u = 0; u < kCompUnroll; ++u) {
             const int l = g0 + u;
             ph[u] = l < a.L ? __ldg(a.phase + l) : make_uint2(0u, 0u);
+            if (VEC) {
+                const int k0 = 64 * g + 2 * lane;   // k0 + 1 < Nk whenever k0 < Nk (Nk even)
+                v[u][0] = v[u][1] = make_float2(0.f, 0.f);
+                if (l < a.L && k0 < Nk) load_echo2<DT>(a.echo, ((long long)l * Nk + k0) >> 1, scale, v[u][0], v[u][1]);
+            } else {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = 64 * g + 32 * h + lane;
-                v[u][h] = (l < a.L && k < Nk) ? load_echo<DT>(a.echo, (long long)l * Nk + k, scale)
-                                              : make_float2(0.f, 0.f);
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 64 * g + 32 * h + lane;
+                    v[u][h] = (l < a.L && k < Nk) ? load_echo<DT>(a.echo, (long long)l * Nk + k, scale)
+                                                  : make_float2(0.f, 0.f);
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
             const int l = g0 + u;
             if (l >= a.L) continue;
-            float2 *dst = a.shat + ((long long)g * a.L + l) * (2 * kKC) + lane;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = 64 * g + 32 * h + lane;
-                float2 out = make_float2(0.f, 0.f);
-                if (k < Nk) {
-                    bad |= !(isfinite(v[u][h].x) && isfinite(v[u][h].y));
-                    const uint32_t turns = ph[u].x + (uint32_t)k * ph[u].y;            // exact mod 2^32
-                    // the angle is already reduced to [-pi, pi): the hardware sine and
-                    // cosine (absolute error ~4e-7 there) are accurate enough
-                    const float ang = (float)(int32_t)turns * 1.4629180792671596e-09f;  // 2 pi turns / 2^32
-                    float sn, cs;
-                    __sincosf(ang, &sn, &cs);
-                    out = cmul(v[u][h], make_float2(cs, sn));
+            if (VEC) {
+                const int k0 = 64 * g + 2 * lane;
+                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k0 < Nk) {
+                    bad |= !(isfinite(v[u][0].x) && isfinite(v[u][0].y) && isfinite(v[u][1].x) && isfinite(v[u][1].y));
+                    const uint32_t t0 = ph[u].x + (uint32_t)k0 * ph[u].y;   // exact mod 2^32
+                    const float2 o0 = rotate_turns(v[u][0], t0), o1 = rotate_turns(v[u][1], t0 + ph[u].y);
+                    out = make_float4(o0.x, o0.y, o1.x, o1.y);
                 }
-                __stcs(dst + 32 * h, out);
+                __stcs(reinterpret_cast<float4 *>(a.shat) + ((long long)g * a.L + l) * kKC + lane, out);
+            } else {
+                float2 *dst = a.shat + ((long long)g * a.L + l) * (2 * kKC) + lane;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 64 * g + 32 * h + lane;
+                    float2 out = make_float2(0.f, 0.f);
+                    if (k < Nk) {
+                        bad |= !(isfinite(v[u][h].x) && isfinite(v[u][h].y));
+                        out = rotate_turns(v[u][h], ph[u].x + (uint32_t)k * ph[u].y);   // exact mod 2^32
+                    }
+                    __stcs(dst + 32 * h, out);
+                }
             }
         }
     }
@@ -584,15 +632,21 @@ cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const f
     a.err = &hdr->error;
     a.shat = reinterpret_cast<float2 *>(w + p.off_shat);
     const unsigned blocks = (unsigned)(a.n_sort_blocks + cb * ((p.n_kc + 1) / 2));
+    // paired loads need an even Nk and an echo aligned to one pair
+    const size_t pair_bytes = p.shape.dtype == MMSAR_ECHO_C64 ? 16 : 8;
+    const bool vec = p.shape.n_k % 2 == 0 && reinterpret_cast<uintptr_t>(echo) % pair_bytes == 0;
     switch (p.shape.dtype) {
         case MMSAR_ECHO_C64:
-            compensate_kernel<MMSAR_ECHO_C64><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            if (vec) compensate_kernel<MMSAR_ECHO_C64, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            else compensate_kernel<MMSAR_ECHO_C64, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
         case MMSAR_ECHO_F16X2_SCALED:
-            compensate_kernel<MMSAR_ECHO_F16X2_SCALED><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            if (vec) compensate_kernel<MMSAR_ECHO_F16X2_SCALED, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            else compensate_kernel<MMSAR_ECHO_F16X2_SCALED, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
         default:
-            compensate_kernel<MMSAR_ECHO_BF16X2_SCALED><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            if (vec) compensate_kernel<MMSAR_ECHO_BF16X2_SCALED, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+            else compensate_kernel<MMSAR_ECHO_BF16X2_SCALED, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
             break;
     }
     return cudaGetLastError();
