@@ -109,17 +109,48 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
             // the Gaussian weights of consecutive points follow the recurrence
             // w_{i+1} = w_i r_i, r_{i+1} = r_i exp(-2 kappa).
             const int nv = a.nk - kf;
+            // grid position of sample k (as sample() computes it)
+            auto grid_pos = [&](int k) {
+                const float kv = wavenumber(k);
+                return sqrtf(4.f * kv * kv - kr2) * cells_per_kz;
+            };
+            // runs of equal sample counts; lanes past the last run are idle
             const int per = (nv + 31) / 32;
-            const int k_beg = kf + lane * per, k_end = min(a.nk, k_beg + per);
-            const bool act = k_beg < k_end;
+            int k_beg = kf + lane * per, k_end = min(a.nk, k_beg + per);
+            int nact = (nv + per - 1) / per;
             int jl = 0x7fffffff;
             bool fits = true;
-            if (act) {
-                const float kv0 = wavenumber(k_beg), kv1 = wavenumber(k_end - 1);
-                const float t0 = sqrtf(4.f * kv0 * kv0 - kr2) * cells_per_kz;
-                const float t1 = sqrtf(4.f * kv1 * kv1 - kr2) * cells_per_kz;
-                jl = (int)ceilf(t0 - hw);
-                fits = (int)ceilf(t1 - hw) + a.w - 1 - jl + 1 <= WR;
+            if (k_beg < k_end) {
+                jl = (int)ceilf(grid_pos(k_beg) - hw);
+                fits = (int)ceilf(grid_pos(k_end - 1) - hw) + a.w - 1 - jl + 1 <= WR;
+            }
+            if (!__all_sync(0xffffffffu, fits)) {
+                // near the evanescent edge k_z rises steeply and equal counts
+                // span unequal depths: split the depth range into 32 equal
+                // spans instead, lane l taking the samples with grid position
+                // in [t_lo + l D, t_lo + (l + 1) D).  A boundary is the first
+                // sample at or past its target, found from the closed-form
+                // inverse of the k -> k_z map and corrected against grid_pos
+                // itself, so neighbouring lanes agree on it exactly.
+                const float t_lo = grid_pos(kf), D = (grid_pos(a.nk - 1) - t_lo) * (1.0f / 32.0f);
+                auto first_at = [&](int m) {
+                    if (m <= 0) return kf;
+                    if (m >= 32) return a.nk;
+                    const float target = fmaf((float)m, D, t_lo);
+                    const float kz = target / cells_per_kz;
+                    int k = (int)ceilf((0.5f * sqrtf(kz * kz + kr2) - k0_hi - k0_lo) / dkf);
+                    k = min(max(k, kf), a.nk);
+                    while (k > kf && grid_pos(k - 1) >= target) --k;
+                    while (k < a.nk && grid_pos(k) < target) ++k;
+                    return k;
+                };
+                k_beg = first_at(lane);
+                k_end = first_at(lane + 1);
+                nact = 32;
+                // an empty run keeps a window start in order with its neighbours
+                const float t_beg = k_beg < k_end ? grid_pos(k_beg) : fmaf((float)lane, D, t_lo);
+                jl = (int)ceilf(t_beg - hw);
+                fits = k_beg >= k_end || (int)ceilf(grid_pos(k_end - 1) - hw) + a.w - 1 - jl + 1 <= WR;
             }
             if (__all_sync(0xffffffffu, fits)) {
                 float2 acc[WR];
@@ -147,7 +178,6 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
                 jlo_s[warp * 32 + lane] = jl;
                 __syncwarp();
                 // sum the windows per grid point, lanes in a fixed order
-                const int nact = (nv + per - 1) / per;
                 const int *jw = jlo_s + warp * 32;
                 const float2 *wb = scratch;
                 const int J_lo = jw[0], J_hi = jw[nact - 1] + WR - 1;

@@ -165,6 +165,28 @@ def test_peak_utility(dev, tiny_scan):
     assert mag == pytest.approx(np.abs(got).max(), rel=1e-6)
 
 
+def test_largest_spectral_grid(dev):
+    """Mx = 1024, the largest spectral grid: the FFT along x' runs at length
+    2048 (the shared-memory kernel) and the inverse along k_x at 1024 (the
+    register kernel's largest length)."""
+    scan = synth.custom(nx_pos=5, ny_pos=4, nk=8, layout="tiny", nx=1024, ny=16, nz=8, seed=31,
+                        jitter=(0.5e-3, 1e-3))
+    got, plan = run_gpu(scan, dev)
+    assert (plan.mx, plan.my) == (1024, 16)
+    assert_parity(got, oracle_of(scan), plan.kernel_width)
+
+
+@pytest.mark.slow
+def test_large_full_size_against_fast_oracle(dev):
+    """The large configuration at full size (3 Tx x 4 Rx, 256 x 256 positions,
+    Nk = 512, 512 x 512 x 128 voxels) against the FP64 fast oracle."""
+    scan = synth.large(n_points=50)
+    got, plan = run_gpu(scan, dev)
+    ref = rma.rma_fast(rma.setup_from(scan), w=12)
+    e = assert_parity(got, ref, plan.kernel_width)
+    assert e < 1e-6
+
+
 @pytest.mark.slow
 def test_realistic_full_size_against_fast_oracle(dev):
     """The full 2Tx x 4Rx, 128x128-position, Nk = 256 scan imaged onto the
