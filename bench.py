@@ -437,8 +437,9 @@ def run_ours(args, dist):
         "gpu_launches": plan.kernels_per_image * args.steps,
         "clocks": clk,
         "grid_launch_shape": {"freqs_per_lane": plan.tiles[0], "warps_per_cta": plan.tiles[1],
+                              "grouped": plan.tiles[2],
                               "autotuned_ms": None if tuned is None else
-                              {f"{a}x{b}": round(v, 4) for (a, b), v in tuned["ms"].items()}},
+                              {f"{a}x{b}{'g' if c else ''}": round(v, 4) for (a, b, c), v in tuned["ms"].items()}},
     }
     return res, scan, vol
 
@@ -593,7 +594,7 @@ def run_batch(args, dist):
     best = ms["graph"]
     shapes = {}
     for t in tuned:
-        key = f"{t['tiles'][0]} freq/lane, {t['tiles'][1]} warps"
+        key = f"{t['tiles'][0]} freq/lane, {t['tiles'][1]} warps" + (", grouped" if t['tiles'][2] else "")
         shapes[key] = shapes.get(key, 0) + 1
     n_img = len(jobs) * dist.world
     return {"metric": "images/s, batched uneven mix (64 scans, 32x32..128x160 positions, Nk 64-256)",

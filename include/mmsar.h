@@ -115,12 +115,19 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
                              int *kernels_per_image);
 
 /* Launch shape of the gridding stage (the spreading step of Sec. III's
- * Gaussian gridding).  Every shape computes the same image, bit for bit
- * within one shape; they differ only in speed, which depends on the scan's
- * size (small scans fill the GPU better with smaller CTAs).  Defaults: 2, 8. */
+ * Gaussian gridding).  The shapes compute the same image: bit for bit among
+ * the per-sample shapes, to rounding between the per-sample and the grouped
+ * form (another summation order); they differ in speed, which depends on the
+ * scan (small scans fill the GPU better with smaller CTAs; arrays whose Tx
+ * and Rx lie on one line along y give large groups).  Defaults: 2, 8, 0. */
 typedef struct {
     int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64           */
     int grid_warps_per_cta;    /* 4: an 8 x 8-cell tile; 8: a 16 x 8-cell tile     */
+    int grid_grouped;          /* 1: the samples of one position whose Tx/Rx pairs *
+                                * share the x offset (Eq. 3: the same x') are     *
+                                * gridded together, the x weights applied once to *
+                                * their y-weighted sum (needs n_tx n_rx <= 16);   *
+                                * 0: sample by sample                              */
 } mmsar_tiles;
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the

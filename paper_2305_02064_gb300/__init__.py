@@ -89,16 +89,17 @@ class Plan:
             self._lib.mmsar_plan_destroy(h)
             self._h = None
 
-    def set_tiles(self, freqs_per_lane: int, warps_per_cta: int):
+    def set_tiles(self, freqs_per_lane: int, warps_per_cta: int, grouped: int = 0):
         """Gridding launch shape (see mmsar_plan_set_tiles; tune.autotune picks one)."""
-        _lib.check(self._lib.mmsar_plan_set_tiles(self._h, ctypes.byref(_lib.Tiles(int(freqs_per_lane),
-                                                                                 int(warps_per_cta)))))
+        _lib.check(self._lib.mmsar_plan_set_tiles(self._h, ctypes.byref(
+            _lib.Tiles(int(freqs_per_lane), int(warps_per_cta), int(grouped)))))
 
     @property
     def tiles(self):
+        """(frequencies per lane, warps per CTA, grouped) of the gridding launch."""
         t = _lib.Tiles()
         _lib.check(self._lib.mmsar_plan_get_tiles(self._h, ctypes.byref(t)))
-        return (t.grid_freqs_per_lane, t.grid_warps_per_cta)
+        return (t.grid_freqs_per_lane, t.grid_warps_per_cta, t.grid_grouped)
 
     @property
     def volume_shape(self):

@@ -55,7 +55,8 @@ class Grid(ctypes.Structure):
 
 
 class Tiles(ctypes.Structure):
-    _fields_ = [("grid_freqs_per_lane", ctypes.c_int), ("grid_warps_per_cta", ctypes.c_int)]
+    _fields_ = [("grid_freqs_per_lane", ctypes.c_int), ("grid_warps_per_cta", ctypes.c_int),
+                ("grid_grouped", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):

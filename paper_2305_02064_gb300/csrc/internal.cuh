@@ -35,9 +35,27 @@ struct WsHeader {
     int geom_done;      // blocks of the geometry pass that have finished
     double inv_4zc;     // 1 / (4 Z_c), Z_c = z_scene - z_ref (0 without compensation)
     double zc;          // Z_c (0 without compensation)
-    double pad[7];
+    // grouped gridding: x-offset classes of the Tx/Rx pairs, and the largest
+    // span of first y cells inside one group
+    int n_classes, vspan_max;
+    double pad[6];
 };
 static_assert(sizeof(WsHeader) == 128, "header size");
+
+// Per-group record of the grouped gridding path: the samples of one position
+// whose Tx/Rx pairs have the same x offset share x' (Eq. 3) and so the x
+// weights; they differ in y.
+struct GroupRec {
+    int u0;             // first x cell, wrapped into [0, Mr)
+    int v0min;          // first y cell of the group's lowest element, wrapped
+    float fx;           // x position minus u0, in cells
+    int vspan;          // highest minus lowest first y cell of its elements
+};
+
+// Largest Tx x Rx pair count of the grouped gridding path: a group's member
+// offsets (first y cell above the group's lowest, 16 bits each) fit one
+// 32-byte record.
+constexpr int kMaxPairsGrouped = 16;
 
 // Per-sample gridding record (sorted by bin).
 struct SampleRec {
@@ -60,6 +78,8 @@ struct Plan {
     int nbx, nby;       // bins per axis (mrx / 4, mry / 4)
     int spread_nf;      // gridding launch shape: frequencies per lane (1 or 2)
     int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells)
+    bool grouped;       // gridding by groups of samples sharing x' (else per sample)
+    int64_t G;          // group slots: n_tx n_rx n_pos (every class may be a single pair)
     int64_t n_bins;
     bool zref_given;
     double z_ref;       // when given
@@ -69,6 +89,11 @@ struct Plan {
     size_t off_counts, off_offsets, off_cursor, off_binid, off_rec, off_phase, off_perm;
     size_t off_dd, off_wq;   // per sorted sample: (in-bin cell offset, sample index); Gaussian weight quads
     size_t off_partials;     // per-block sums of the z_ref reduction
+    size_t off_cls;          // pair classes [TR], class starts [TR + 1], members [TR]
+    size_t off_grec;         // per group: GroupRec [G]
+    size_t off_gdd, off_gxq; // per sorted group: (in-bin offsets, group index); x weight quads [w + 3]
+    size_t off_goff;         // per sorted group: its members' y offsets, uint16 x 16
+    size_t off_yq;           // per sample (original order): offset header + y weight quads [w + 4]
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
     // optional per-stage timing events (caller-owned)
@@ -96,6 +121,7 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s);

@@ -131,6 +131,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.n_bins = (int64_t)p.nbx * p.nby;
     p.spread_nf = 2;
     p.spread_warps = 8;
+    p.grouped = false;
+    p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;
     p.z_scene = std::isfinite(o.z_scene) ? o.z_scene : g.z0 + 0.5 * (g.nz - 1) * g.dz;
@@ -159,6 +161,13 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_perm = take(sizeof(int) * L);
     p.off_dd = take(sizeof(int2) * L);
     p.off_wq = take(sizeof(float4) * (size_t)(2 * p.w + 7) * L);
+    const size_t TR = (size_t)sh.n_tx * sh.n_rx;
+    p.off_cls = take(sizeof(int) * (3 * TR + 1));
+    p.off_grec = take(sizeof(GroupRec) * (size_t)p.G);
+    p.off_gdd = take(sizeof(int2) * (size_t)p.G);
+    p.off_gxq = take(sizeof(float4) * (size_t)(p.w + 3) * (size_t)p.G);
+    p.off_goff = take(2 * sizeof(int4) * (size_t)p.G);
+    p.off_yq = take(sizeof(float4) * (size_t)(p.w + 4) * L);
     p.off_shat = take(sizeof(float2) * (size_t)((p.n_kc + 1) / 2) * L * 2 * kKC);   // 64-frequency groups
     const size_t G = sizeof(float2) * (size_t)p.n_kc * p.mry * p.mrx * kKC;
     const size_t S = sizeof(float2) * (size_t)p.mx * p.my * p.nkp;
@@ -234,8 +243,13 @@ mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
         return fail(MMSAR_ERR_INVALID_ARG, "grid_freqs_per_lane must be 1 or 2");
     if (tiles->grid_warps_per_cta != 4 && tiles->grid_warps_per_cta != 8)
         return fail(MMSAR_ERR_INVALID_ARG, "grid_warps_per_cta must be 4 or 8");
+    if (tiles->grid_grouped != 0 && tiles->grid_grouped != 1)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_grouped must be 0 or 1");
+    if (tiles->grid_grouped && (int64_t)plan->p.shape.n_tx * plan->p.shape.n_rx > kMaxPairsGrouped)
+        return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "grouped gridding takes at most %d Tx/Rx pairs", kMaxPairsGrouped);
     plan->p.spread_nf = tiles->grid_freqs_per_lane;
     plan->p.spread_warps = tiles->grid_warps_per_cta;
+    plan->p.grouped = tiles->grid_grouped != 0;
     return MMSAR_OK;
 }
 
@@ -243,6 +257,7 @@ mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles) {
     if (!plan || !tiles) return fail(MMSAR_ERR_INVALID_ARG, "null plan or tiles");
     tiles->grid_freqs_per_lane = plan->p.spread_nf;
     tiles->grid_warps_per_cta = plan->p.spread_warps;
+    tiles->grid_grouped = plan->p.grouped ? 1 : 0;
     return MMSAR_OK;
 }
 
@@ -302,7 +317,7 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_MARK(1);
     MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation, bin sort and gridding weights");
     MMSAR_MARK(2);
-    MMSAR_STEP(launch_spread(p, workspace, s), "gridding");
+    MMSAR_STEP(p.grouped ? launch_spread_groups(p, workspace, s) : launch_spread(p, workspace, s), "gridding");
     MMSAR_MARK(3);
     MMSAR_STEP(launch_fft_x(p, workspace, s), "FT_2D along x'");
     MMSAR_MARK(4);

@@ -44,18 +44,81 @@ __device__ __forceinline__ void resolve_zref(double z_ref, double z_scene, int c
     hdr->zc = (compensate && Zc > 0.0) ? Zc : 0.0;
 }
 
+// Classes of the Tx/Rx pairs for the grouped gridding: pairs whose x offsets
+// sum to the same value (tx_x + rx_x, compared exactly) put their virtual
+// elements at the same x' for every position (Eq. 3).  Classes are numbered
+// in order of first appearance; the tables hold the class of each pair, the
+// start of each class in the member list and the members in ascending pair
+// order.  One block, every thread of it (pairs <= kMaxPairsGrouped <= threads).
+static_assert(kMaxPairsGrouped <= kZrefThreads, "one thread per pair");
+
+__device__ void pair_classes(const double *__restrict__ tx, const double *__restrict__ rx, int T, int R,
+                             int *cls, WsHeader *hdr) {
+    __shared__ double xo[kMaxPairsGrouped];
+    __shared__ int pc[kMaxPairsGrouped];
+    const int TR = T * R, tid = threadIdx.x;
+    if (TR > kMaxPairsGrouped) {
+        if (tid == 0) hdr->n_classes = 0;
+        return;
+    }
+    if (tid < TR) xo[tid] = tx[3 * (tid / R)] + rx[3 * (tid % R)];
+    __syncthreads();
+    // representative: the first pair with the same offset; the class number
+    // is the count of representatives before it
+    int rep = tid;
+    if (tid < TR)
+        for (int q = 0; q < tid; ++q)
+            if (xo[q] == xo[tid]) {
+                rep = q;
+                break;
+            }
+    __syncthreads();
+    if (tid < TR) pc[tid] = rep == tid ? 1 : 0;   // representative flags
+    __syncthreads();
+    int c = 0, n_cls = 0;
+    if (tid < TR) {
+        for (int q = 0; q < TR; ++q) {
+            n_cls += pc[q];
+            if (q < rep) c += pc[q];
+        }
+    }
+    __syncthreads();
+    if (tid < TR) pc[tid] = c;
+    __syncthreads();
+    int *pclass = cls, *start = cls + TR, *members = cls + 2 * TR + 1;
+    if (tid < TR) {
+        // members of the classes before c, then the pairs of class c before this one
+        int pos = 0;
+        for (int q = 0; q < TR; ++q) pos += (pc[q] < c) || (pc[q] == c && q < tid);
+        members[pos] = tid;
+        pclass[tid] = c;
+        if (rep == tid) {
+            int before = 0;
+            for (int q = 0; q < TR; ++q) before += pc[q] < c;
+            start[c] = before;
+        }
+        if (tid == 0) {
+            start[n_cls] = TR;
+            hdr->n_classes = n_cls;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__restrict__ pos, int P,
                                                             const double *__restrict__ tx, int T,
                                                             const double *__restrict__ rx, int R, int given,
                                                             double z_given, double z_scene, int compensate,
-                                                            double *partials, WsHeader *hdr) {
+                                                            double *partials, int *cls, WsHeader *hdr) {
     __shared__ double red[kZrefThreads];
     __shared__ bool last;
     const int tid = threadIdx.x;
-    if (blockIdx.x == 0 && tid == 0) {
-        hdr->u_min = hdr->v_min = 0x7fffffff;
-        hdr->u_max = hdr->v_max = -0x7fffffff - 1;
-        if (given) resolve_zref(z_given, z_scene, compensate, hdr);
+    if (blockIdx.x == 0) {
+        if (tid == 0) {
+            hdr->u_min = hdr->v_min = 0x7fffffff;
+            hdr->u_max = hdr->v_max = -0x7fffffff - 1;
+            if (given) resolve_zref(z_given, z_scene, compensate, hdr);
+        }
+        pair_classes(tx, rx, T, R, cls, hdr);
     }
     if (given) return;
     const int per = (P + gridDim.x - 1) / gridDim.x;
@@ -102,7 +165,8 @@ cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double
     if (p.zref_given) blocks = 1;
     zref_kernel<<<blocks, kZrefThreads, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
                                                 p.zref_given ? 1 : 0, p.z_ref, p.z_scene, p.opt.compensate,
-                                                reinterpret_cast<double *>(w + p.off_partials), hdr);
+                                                reinterpret_cast<double *>(w + p.off_partials),
+                                                reinterpret_cast<int *>(w + p.off_cls), hdr);
     return cudaGetLastError();
 }
 
@@ -123,6 +187,10 @@ struct GeomArgs {
     int *binid;
     SampleRec *rec;
     uint2 *phase;
+    // grouped gridding: bins hold groups (class, position) instead of samples
+    int grouped, G;
+    const int *cls;          // pair classes (see pair_classes)
+    GroupRec *grec;
 };
 
 // A phase given as turns x 2^32 -> 32-bit fixed-point turns: the low 32 bits
@@ -151,7 +219,9 @@ __device__ __forceinline__ void box_reduce(int umin, int umax, int vmin, int vma
 }
 
 // Returns the sample's bin (-1 when it is not binned); the caller counts it.
-__device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int &vmin, int &vmax) {
+// With bin_it false (grouped gridding) the sample is neither binned nor part
+// of the occupied window: its group is.
+__device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int &vmin, int &vmax, bool bin_it) {
     const int tr = l / a.P, p = l - tr * a.P;
     const int t = tr / a.R, r = tr - t * a.R;
     const double px = a.pos[3 * p], py = a.pos[3 * p + 1], pz = a.pos[3 * p + 2];
@@ -164,7 +234,7 @@ __device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int 
     const double z_ref = a.hdr->z_ref, inv_4zc = a.hdr->inv_4zc;
     if (!(isfinite(xv) && isfinite(yv) && isfinite(zl))) {
         atomicOr(&a.hdr->error, kErrNonfinite);
-        a.binid[l] = -1;
+        if (bin_it) a.binid[l] = -1;
         return -1;
     }
     // residual of the round trip over 2 R_0 (Z_c <= 0 was flagged once when
@@ -192,10 +262,12 @@ __device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int 
     // occupied window; a sample absurdly far away (beyond 1e9 cells) makes the
     // window the whole grid
     const bool ufar = fabs(u0d) > 1.0e9, vfar = fabs(v0d) > 1.0e9;
-    umin = ufar ? -1073741824 : (int)u0d;
-    umax = ufar ? 1073741823 : (int)u0d;
-    vmin = vfar ? -1073741824 : (int)v0d;
-    vmax = vfar ? 1073741823 : (int)v0d;
+    if (bin_it) {
+        umin = ufar ? -1073741824 : (int)u0d;
+        umax = ufar ? 1073741823 : (int)u0d;
+        vmin = vfar ? -1073741824 : (int)v0d;
+        vmax = vfar ? 1073741823 : (int)v0d;
+    }
     // wrap into [0, M_r) (M_r is a power of two; beyond 2^62 cells the
     // position is meaningless and is put at cell 0)
     const long long u0l = fabs(u0d) < 4.0e18 ? (long long)u0d : 0;
@@ -209,8 +281,61 @@ __device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int 
     a.rec[l] = rc;
     // Eq. 11 phase k beta = 2 pi f beta / c in turns: f0 beta/c + k df beta/c
     a.phase[l] = make_uint2(turns32_to_fixed(a.f0_over_c32 * beta), turns32_to_fixed(a.df_over_c32 * beta));
+    if (!bin_it) return -1;
     const int bin = (rc.v0 / kBin) * a.nbx + rc.u0 / kBin;
     a.binid[l] = bin;
+    return bin;
+}
+
+// Group g = (class c, position p) of the grouped gridding: the class's shared
+// x' (computed as its first member's sample does) gives the x cell; the
+// lowest and highest first y cell of its members (computed as their samples
+// do) give the group's y extent.  Returns the group's bin (-1: no group).
+__device__ int group_one(const GeomArgs &a, int g, int &umin, int &umax, int &vmin, int &vmax, int &vspan) {
+    const int TR = a.T * a.R;
+    const int c = g / a.P, p = g - c * a.P;
+    if (c >= a.hdr->n_classes) {
+        a.binid[g] = -1;
+        return -1;
+    }
+    const int *start = a.cls + TR, *members = a.cls + 2 * TR + 1;
+    const int m_beg = start[c], m_end = start[c + 1];
+    const int m0 = members[m_beg], t0 = m0 / a.R, r0 = m0 - t0 * a.R;
+    const double px = a.pos[3 * p], py = a.pos[3 * p + 1];
+    const double xv = 0.5 * ((px + a.tx[3 * t0]) + (px + a.rx[3 * r0]));
+    bool ok = isfinite(xv);
+    double vlo = 0.0, vhi = 0.0;
+    for (int m = m_beg; m < m_end; ++m) {
+        const int tr = members[m], t = tr / a.R, r = tr - t * a.R;
+        const double yv = 0.5 * ((py + a.tx[3 * t + 1]) + (py + a.rx[3 * r + 1]));
+        ok = ok && isfinite(yv);
+        const double v0d = ceil((yv - a.y_c) * a.inv_dy2 - a.half_w);
+        vlo = m == m_beg ? v0d : fmin(vlo, v0d);
+        vhi = m == m_beg ? v0d : fmax(vhi, v0d);
+    }
+    if (!ok) {
+        atomicOr(&a.hdr->error, kErrNonfinite);
+        a.binid[g] = -1;
+        return -1;
+    }
+    const double gx = (xv - a.x_c) * a.inv_dx2;
+    const double u0d = ceil(gx - a.half_w);
+    const bool ufar = fabs(u0d) > 1.0e9, vfar = fabs(vlo) > 1.0e9 || fabs(vhi) > 1.0e9;
+    umin = ufar ? -1073741824 : (int)u0d;
+    umax = ufar ? 1073741823 : (int)u0d;
+    vmin = vfar ? -1073741824 : (int)vlo;
+    vmax = vfar ? 1073741823 : (int)vhi;
+    const long long u0l = fabs(u0d) < 4.0e18 ? (long long)u0d : 0;
+    const long long v0l = fabs(vlo) < 4.0e18 ? (long long)vlo : 0;
+    GroupRec gr;
+    gr.u0 = (int)(u0l & (a.mrx - 1));
+    gr.v0min = (int)(v0l & (a.mry - 1));
+    gr.fx = (float)(gx - u0d);
+    gr.vspan = vfar ? 0 : (int)fmin(vhi - vlo, (double)(a.mry - 1));
+    a.grec[g] = gr;
+    vspan = gr.vspan;
+    const int bin = (gr.v0min / kBin) * a.nbx + gr.u0 / kBin;
+    a.binid[g] = bin;
     return bin;
 }
 
@@ -222,7 +347,15 @@ __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
     __shared__ bool last;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     int bumin = 0x7fffffff, bumax = -0x7fffffff - 1, bvmin = 0x7fffffff, bvmax = -0x7fffffff - 1;
-    const int bin = l < a.L ? geometry_one(a, l, bumin, bumax, bvmin, bvmax) : -1;
+    int bin = -1, vspan = 0;
+    if (l < a.L)
+        bin = geometry_one(a, l, bumin, bumax, bvmin, bvmax, !a.grouped);
+    else if (a.grouped && l - a.L < a.G)
+        bin = group_one(a, l - a.L, bumin, bumax, bvmin, bvmax, vspan);
+    if (a.grouped) {   // the largest group span, one atomic per warp
+        for (int o = 16; o > 0; o >>= 1) vspan = max(vspan, __shfl_xor_sync(0xffffffffu, vspan, o));
+        if ((threadIdx.x & 31) == 0 && vspan > 0) atomicMax(&a.hdr->vspan_max, vspan);
+    }
     // neighbouring samples share bins: one atomic per distinct bin of the warp
     const unsigned grp = __match_any_sync(0xffffffffu, bin);
     if (bin >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.counts[bin], __popc(grp));
@@ -270,7 +403,12 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
     a.binid = reinterpret_cast<int *>(w + p.off_binid);
     a.rec = reinterpret_cast<SampleRec *>(w + p.off_rec);
     a.phase = reinterpret_cast<uint2 *>(w + p.off_phase);
-    const unsigned blocks = (unsigned)((p.L + 255) / 256);
+    a.grouped = p.grouped ? 1 : 0;
+    a.G = (int)p.G;
+    a.cls = reinterpret_cast<const int *>(w + p.off_cls);
+    a.grec = reinterpret_cast<GroupRec *>(w + p.off_grec);
+    const long long threads = p.L + (p.grouped ? p.G : 0);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
     geometry_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -385,8 +523,9 @@ __global__ void __launch_bounds__(256) bin_scatter_kernel(int L, const int *__re
 
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
     char *w = reinterpret_cast<char *>(ws);
-    const unsigned blocks = (unsigned)((p.L + 255) / 256);
-    bin_scatter_kernel<<<blocks, 256, 0, s>>>((int)p.L, reinterpret_cast<int *>(w + p.off_binid),
+    const long long items = p.grouped ? p.G : p.L;   // groups or samples
+    const unsigned blocks = (unsigned)((items + 255) / 256);
+    bin_scatter_kernel<<<blocks, 256, 0, s>>>((int)items, reinterpret_cast<int *>(w + p.off_binid),
                                               reinterpret_cast<int *>(w + p.off_cursor),
                                               reinterpret_cast<int *>(w + p.off_perm));
     return cudaGetLastError();
@@ -411,6 +550,76 @@ cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
 constexpr int kSortBinCap = 256;
 constexpr int kPrepWarps = 8;
 
+// Gaussian weights exp(-kappa (f - tap)^2) of taps q-3 .. q (zero outside
+// 0 .. w-1): the four weights a 4-cell block needs when it starts q - 3 cells
+// after the first tap.
+__device__ __forceinline__ float4 weight_quad(float f, int q, int w, float kappa) {
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int tap = q - 3 + i;
+        const float dlt = f - (float)tap;
+        v[i] = (tap >= 0 && tap < w) ? expf(-kappa * dlt * dlt) : 0.f;
+    }
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Rank sort of one bin's entries (perm[beg .. beg + n)) into ascending order
+// in shared memory when the bin holds at most kSortBinCap of them (larger
+// bins keep the arrival order: still correct, only the last bits of the
+// image can then vary between runs).  Returns whether it sorted.
+__device__ bool sort_bin(int *pp, int n, int *keys, int *sorted) {
+    const int lane = threadIdx.x & 31;
+    if (n > kSortBinCap) return false;
+    for (int i = lane; i < n; i += 32) keys[i] = pp[i];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int ki = keys[i];
+        int rank = 0;   // #{j : key_j < key_i}; the entries are distinct
+        for (int j = 0; j < n; ++j) rank += keys[j] < ki;
+        sorted[rank] = ki;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) pp[i] = sorted[i];
+    return true;
+}
+
+// Grouped gridding: one bin of groups in ascending group order, and per group
+// in that order its in-bin offsets with its index, and its w + 3 x weight quads.
+__device__ void sort_and_weigh_group_bin(int b, const int *__restrict__ offsets, int *__restrict__ perm,
+                                         const GroupRec *__restrict__ grec, int w, float kappa,
+                                         int2 *__restrict__ gdd, float4 *__restrict__ gxq, int4 *__restrict__ goff,
+                                         const SampleRec *__restrict__ rec, const int *__restrict__ cls, int TR,
+                                         int P, int mry, int *keys, int *sorted) {
+    const int lane = threadIdx.x & 31;
+    const int beg = offsets[b], n = offsets[b + 1] - beg;
+    if (n == 0) return;
+    int *pp = perm + beg;
+    const bool small = sort_bin(pp, n, keys, sorted);
+    const int nq = w + 3;
+    const int total = n * nq;
+    for (int e = lane; e < total; e += 32) {
+        const int sl = e / nq, q = e - sl * nq;
+        const int g = small ? sorted[sl] : pp[sl];
+        const GroupRec r = grec[g];
+        if (q == 0) {
+            gdd[beg + sl] = make_int2((r.u0 & 3) | ((r.v0min & 3) << 2), g);
+            // the members' first y cells above the group's lowest, 16 bits each
+            const int c = g / P, pp = g - c * P;
+            const int *start = cls + TR, *members = cls + 2 * TR + 1;
+            unsigned o[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            for (int m = start[c]; m < start[c + 1]; ++m) {
+                const int k = m - start[c];
+                const unsigned off = (unsigned)((rec[members[m] * P + pp].v0 - r.v0min) & (mry - 1)) & 0xffffu;
+                o[k >> 1] |= off << (16 * (k & 1));
+            }
+            goff[2 * (beg + sl)] = make_int4((int)o[0], (int)o[1], (int)o[2], (int)o[3]);
+            goff[2 * (beg + sl) + 1] = make_int4((int)o[4], (int)o[5], (int)o[6], (int)o[7]);
+        }
+        gxq[(long long)(beg + sl) * nq + q] = weight_quad(r.fx, q, w, kappa);
+    }
+}
+
 __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *__restrict__ perm,
                                    const SampleRec *__restrict__ rec, int w, float kappa, int2 *__restrict__ dd,
                                    float4 *__restrict__ wrec, int *keys, int *sorted) {
@@ -418,19 +627,7 @@ __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *
     const int beg = offsets[b], n = offsets[b + 1] - beg;
     if (n == 0) return;
     int *pp = perm + beg;
-    const bool small = n <= kSortBinCap;
-    if (small) {
-        for (int i = lane; i < n; i += 32) keys[i] = pp[i];
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const int ki = keys[i];
-            int rank = 0;   // #{j : key_j < key_i}; sample indices are distinct
-            for (int j = 0; j < n; ++j) rank += keys[j] < ki;
-            sorted[rank] = ki;
-        }
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) pp[i] = sorted[i];
-    }
+    const bool small = sort_bin(pp, n, keys, sorted);
     const int nq = w + 3, rq = 2 * nq + 1;
     const int total = n * rq;
     for (int e = lane; e < total; e += 32) {
@@ -444,15 +641,7 @@ __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *
             out = make_float4(__int_as_float(d), __int_as_float(l), 0.f, 0.f);
         } else {
             const int q = (ent - 1) % nq;                 // quad q = taps q-3 .. q
-            const float f = (ent - 1) < nq ? r.fx : r.fy;
-            float v[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int tap = q - 3 + i;
-                const float dlt = f - (float)tap;
-                v[i] = (tap >= 0 && tap < w) ? expf(-kappa * dlt * dlt) : 0.f;
-            }
-            out = make_float4(v[0], v[1], v[2], v[3]);
+            out = weight_quad((ent - 1) < nq ? r.fx : r.fy, q, w, kappa);
         }
         wrec[(long long)(beg + sl) * rq + ent] = out;
     }
@@ -526,6 +715,15 @@ struct PrepTailArgs {
     float kappa;
     int2 *dd;
     float4 *wrec;
+    // grouped gridding: group records, their sorted offsets and x quads, and
+    // per sample (original order) a header with the first-y-cell offset
+    // within its group followed by its y quads
+    int grouped, n_yrec_blocks, P, R, TR, mry;
+    const GroupRec *grec;
+    const int *cls;
+    int2 *gdd;
+    int4 *goff;
+    float4 *gxq, *yq;
     // compensation
     const void *echo;
     const float *scale;
@@ -545,11 +743,36 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if ((int)blockIdx.x < a.n_sort_blocks) {
         const int b = blockIdx.x * kPrepWarps + warp;
-        if (b < a.n_bins)
-            sort_and_weigh_bin(b, a.offsets, a.perm, a.rec, a.w, a.kappa, a.dd, a.wrec, keys[warp], sorted[warp]);
+        if (b < a.n_bins) {
+            if (a.grouped)
+                sort_and_weigh_group_bin(b, a.offsets, a.perm, a.grec, a.w, a.kappa, a.gdd, a.gxq, a.goff, a.rec,
+                                         a.cls, a.TR, a.P, a.mry, keys[warp], sorted[warp]);
+            else
+                sort_and_weigh_bin(b, a.offsets, a.perm, a.rec, a.w, a.kappa, a.dd, a.wrec, keys[warp],
+                                   sorted[warp]);
+        }
         return;
     }
-    const int cblk = blockIdx.x - a.n_sort_blocks;
+    if ((int)blockIdx.x < a.n_sort_blocks + a.n_yrec_blocks) {
+        // grouped gridding, per sample: entry 0 holds the offset of its first
+        // y cell above its group's lowest, entries 1 .. w + 3 its y quads
+        const int rqy = a.w + 4;
+        const long long e = (long long)(blockIdx.x - a.n_sort_blocks) * blockDim.x + threadIdx.x;
+        const long long l = e / rqy;
+        if (l >= a.L) return;
+        const int q = (int)(e - l * rqy);
+        const SampleRec r = a.rec[l];
+        if (q == 0) {
+            const int tr = (int)(l / a.P), pp = (int)(l - (long long)tr * a.P);
+            const int g = a.cls[tr] * a.P + pp;
+            const int off = (r.v0 - a.grec[g].v0min) & (a.mry - 1);
+            a.yq[e] = make_float4(__int_as_float(off), 0.f, 0.f, 0.f);
+        } else {
+            a.yq[e] = weight_quad(r.fy, q - 1, a.w, a.kappa);
+        }
+        return;
+    }
+    const int cblk = blockIdx.x - a.n_sort_blocks - a.n_yrec_blocks;
     const int g = cblk / a.chunk_blocks, bx = cblk - g * a.chunk_blocks;
     const int Nk = a.Nk;
     const int warps = a.chunk_blocks * kPrepWarps;
@@ -620,6 +843,18 @@ cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const f
     a.kappa = (float)(1.5 * kPi / p.w);
     a.dd = reinterpret_cast<int2 *>(w + p.off_dd);
     a.wrec = reinterpret_cast<float4 *>(w + p.off_wq);
+    a.grouped = p.grouped ? 1 : 0;
+    a.n_yrec_blocks = p.grouped ? (int)((p.L * (p.w + 4) + kPrepWarps * 32 - 1) / (kPrepWarps * 32)) : 0;
+    a.P = p.shape.n_pos;
+    a.R = p.shape.n_rx;
+    a.TR = p.shape.n_tx * p.shape.n_rx;
+    a.mry = p.mry;
+    a.goff = reinterpret_cast<int4 *>(w + p.off_goff);
+    a.grec = reinterpret_cast<const GroupRec *>(w + p.off_grec);
+    a.cls = reinterpret_cast<const int *>(w + p.off_cls);
+    a.gdd = reinterpret_cast<int2 *>(w + p.off_gdd);
+    a.gxq = reinterpret_cast<float4 *>(w + p.off_gxq);
+    a.yq = reinterpret_cast<float4 *>(w + p.off_yq);
     a.echo = echo;
     a.scale = scale;
     a.phase = reinterpret_cast<const uint2 *>(w + p.off_phase);
@@ -631,7 +866,7 @@ cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const f
     a.chunk_blocks = (int)cb;
     a.err = &hdr->error;
     a.shat = reinterpret_cast<float2 *>(w + p.off_shat);
-    const unsigned blocks = (unsigned)(a.n_sort_blocks + cb * ((p.n_kc + 1) / 2));
+    const unsigned blocks = (unsigned)(a.n_sort_blocks + a.n_yrec_blocks + cb * ((p.n_kc + 1) / 2));
     // paired loads need an even Nk and an echo aligned to one pair
     const size_t pair_bytes = p.shape.dtype == MMSAR_ECHO_C64 ? 16 : 8;
     const bool vec = p.shape.n_k % 2 == 0 && reinterpret_cast<uintptr_t>(echo) % pair_bytes == 0;

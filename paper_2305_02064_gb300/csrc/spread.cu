@@ -239,3 +239,279 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
 }
 
 }  // namespace mmsar
+
+// ---------------------------------------------------------------- grouped gridding
+// The samples of one position whose Tx/Rx pairs share the x offset (the same
+// x', Eq. 3) share the x weights, so a warp block sums such a group's
+// samples into one y-weighted value per block row first,
+//     T_j = sum_e wy_j(e) s_hat_e,
+// and applies the x weights once per group: acc_ji += wx_i T_j (for the
+// 4 x 4 block, 8 multiply-adds per sample and 16 per group, instead of 16 per
+// sample).  The bins hold groups (by their x cell and their lowest first y
+// cell); a warp tests 32 groups at a time, one lane each, lists the group's
+// samples that reach its rows next to each other (the last one flagged), and
+// applies the list through the same pipeline as the per-sample kernel.
+namespace mmsar {
+
+struct SpreadGroupArgs {
+    const float2 *shat;       // [n_kc / 2][Lmax][64], original sample order
+    const int2 *gdd;          // [G] per sorted group: (du | dv << 2 of its lowest first cell, group)
+    const float4 *gxq;        // [G][w + 3] x quads per sorted group
+    const float4 *yq;         // [Lmax][w + 4] per sample: offset header, y quads
+    const int4 *goff;         // [G][2] per sorted group: members' y offsets, uint16 x 16
+    const int *offsets;       // [n_bins + 1] group bins
+    const int *cls;           // pair classes, class starts, members
+    float2 *G;
+    const WsHeader *hdr;
+    long long Lmax;
+    int P, TR;
+    int mrx, mry, nbx, nby;
+    int w, nb, n_kc;
+};
+
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spread_groups_kernel(SpreadGroupArgs a) {
+    constexpr int TX = 4 * (WARPS / 2);
+    // per warp: (x-quad index, y-quad index, sample index, last of its group)
+    __shared__ int4 lists[WARPS][kListCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tiles_x = a.mrx / TX;
+    const int n_kg = NF == 2 ? (a.n_kc + 1) / 2 : a.n_kc;
+    const int kg = blockIdx.x % n_kg;
+    const int tile = blockIdx.x / n_kg;
+    if (!tile_meets((tile % tiles_x) * TX, TX, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
+        !tile_meets((tile / tiles_x) * 8, 8, a.hdr->v_lo, a.hdr->v_len, a.mry))
+        return;
+    const int U = (tile % tiles_x) * TX + (warp % (WARPS / 2)) * 4;
+    const int V = (tile / tiles_x) * 8 + (warp / (WARPS / 2)) * 4;
+    const int nqx = a.w + 3, rqy = a.w + 4;
+    const int vspan = a.hdr->vspan_max;
+    // bin rows of a group's lowest first y cell that can reach the block rows
+    const int nbv = min((vspan + a.w + 2) / 4 + 1, a.nby);
+    // the class tables in shared memory: class starts, then members
+    __shared__ int ctab[2 * kMaxPairsGrouped + 1];
+    for (int i = threadIdx.x; i < 2 * a.TR + 1; i += blockDim.x) ctab[i] = a.cls[a.TR + i];
+    __syncthreads();
+    const int *cstart = ctab, *members = ctab + a.TR + 1;
+    float2 acc[NF][4][4];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[f][j][i] = make_float2(0.f, 0.f);
+    const int col0 = NF == 2 ? 2 * lane : (kg & 1) * 32 + lane;
+    const float2 *sh = a.shat + (long long)(NF == 2 ? kg : kg >> 1) * a.Lmax * 64 + col0;
+    int4 *list = lists[warp];
+
+    struct Stage {
+        float4 x, y;
+        float2 v[NF];
+        int last;
+    };
+    auto apply = [&](int n) {
+        float2 T[NF][4];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) T[f][j] = make_float2(0.f, 0.f);
+        Stage st[NS];
+        auto fetch = [&](int i, Stage &q) {
+            const int4 e = list[i];
+            q.x = __ldg(a.gxq + e.x);
+            q.y = __ldg(a.yq + e.y);
+            q.last = e.w;
+            if constexpr (NF == 2) {
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(sh) + (e.z << 5));
+                q.v[0] = make_float2(t.x, t.y);
+                q.v[NF - 1] = make_float2(t.z, t.w);
+            } else {
+                q.v[0] = __ldg(sh + ((long long)e.z << 6));
+            }
+        };
+        auto consume = [&](const Stage &q) {
+            const float wy[4] = {q.y.x, q.y.y, q.y.z, q.y.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 wyj = make_float2(wy[j], wy[j]);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) T[f][j] = ffma2(wyj, q.v[f], T[f][j]);
+            }
+            if (q.last) {   // the group is complete: its x weights, once
+                const float wx[4] = {q.x.x, q.x.y, q.x.z, q.x.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 wxi = make_float2(wx[i], wx[i]);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) acc[f][j][i] = ffma2(wxi, T[f][j], acc[f][j][i]);
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) T[f][j] = make_float2(0.f, 0.f);
+            }
+        };
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if (k < n) fetch(k, st[k]);
+        for (int i = 0; i < n; i += NS) {
+#pragma unroll
+            for (int k = 0; k < NS; ++k) {
+                if (i + k >= n) break;
+                consume(st[k]);
+                if (i + k + NS < n) fetch(i + k + NS, st[k]);
+            }
+        }
+    };
+
+    // the candidate groups of all nbv x nb bins around the block, enumerated as
+    // one sequence (bin by bin, in bin order) so that every 32-lane round is
+    // full: lane b < nbins holds bin b's start and its first index in the
+    // sequence.  Bins are visited in chunks of 32.
+    const int bu0 = U >> 2, bv0 = V >> 2;
+    const int nbins = nbv * a.nb;
+    const unsigned lt = (1u << lane) - 1u;
+    int n = 0;
+    for (int b0 = 0; b0 < nbins; b0 += 32) {
+        int beg = 0, cnt_b = 0, dbu = 0, dbv = 0;
+        const int b = b0 + lane;
+        if (b < nbins) {
+            dbv = nbv - 1 - b / a.nb;
+            dbu = a.nb - 1 - (b - (b / a.nb) * a.nb);
+            int bv = bv0 - dbv, bu = bu0 - dbu;
+            if (bv < 0) bv += a.nby;
+            if (bu < 0) bu += a.nbx;
+            const int bin = bv * a.nbx + bu;
+            beg = __ldg(a.offsets + bin);
+            cnt_b = __ldg(a.offsets + bin + 1) - beg;
+        }
+        int first = cnt_b;   // exclusive scan of the bin sizes
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, first, o);
+            if (lane >= o) first += y;
+        }
+        const int n_cand = __shfl_sync(0xffffffffu, first, 31);
+        first -= cnt_b;
+        const int nb_here = min(32, nbins - b0);
+        for (int c0 = 0; c0 < n_cand; c0 += 32) {
+            const int c = c0 + lane;
+            // the bin holding candidate c: the last bin whose first index is <= c
+            int sel = 0;
+            for (int q = 1; q < nb_here; ++q)
+                if (__shfl_sync(0xffffffffu, first, q) <= c) sel = q;
+            const int my = __shfl_sync(0xffffffffu, beg, sel) + c - __shfl_sync(0xffffffffu, first, sel);
+            const int gdbu = __shfl_sync(0xffffffffu, dbu, sel), gdbv = __shfl_sync(0xffffffffu, dbv, sel);
+            // the samples of the lane's group that reach this block (bit k: member k)
+            unsigned mask = 0u;
+            int ru = 0, rvg = 0, p = 0, m_beg = 0;
+            unsigned off[8];
+            if (c < n_cand) {
+                const int2 gd = __ldg(a.gdd + my);
+                ru = 4 * gdbu - (gd.x & 3);     // block start relative to the first x tap, >= -3
+                rvg = 4 * gdbv - (gd.x >> 2);   // block start relative to the lowest first y cell
+                const int cl = gd.y / a.P;
+                p = gd.y - cl * a.P;
+                m_beg = cstart[cl];
+                const int m_cnt = cstart[cl + 1] - m_beg;
+                if (ru < a.w && rvg >= -3 && rvg < vspan + a.w) {
+                    const int4 o0 = __ldg(a.goff + 2 * my), o1 = __ldg(a.goff + 2 * my + 1);
+                    off[0] = o0.x; off[1] = o0.y; off[2] = o0.z; off[3] = o0.w;
+                    off[4] = o1.x; off[5] = o1.y; off[6] = o1.z; off[7] = o1.w;
+#pragma unroll
+                    for (int k = 0; k < kMaxPairsGrouped; ++k) {
+                        const int rv = rvg - (int)((off[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+                        if (k < m_cnt && rv >= -3 && rv < a.w) mask |= 1u << k;
+                    }
+                }
+            }
+            const int cnt = __popc(mask);
+            int base = cnt;   // exclusive scan of the counts over the lanes
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, base, o);
+                if (lane >= o) base += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, base, 31);
+            base -= cnt;
+            if (n + total > kListCap) {   // keep the list within its buffer
+                __syncwarp();
+                apply(n);
+                n = 0;
+                __syncwarp();
+            }
+            int slot = n + base;
+            while (mask) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                // the member's offset: word k / 2, half k % 2 (selected without indexing)
+                unsigned word = off[0];
+#pragma unroll
+                for (int q = 1; q < 8; ++q)
+                    if ((k >> 1) == q) word = off[q];
+                const int rv = rvg - (int)((word >> (16 * (k & 1))) & 0xffffu);
+                const int l = members[m_beg + k] * a.P + p;
+                list[slot++] = make_int4(my * nqx + ru + 3, l * rqy + 1 + rv + 3, l, mask == 0u);
+            }
+            n += total;
+        }
+    }
+    __syncwarp();
+    apply(n);
+    if constexpr (NF == 2) {
+        const int kc = 2 * kg + (lane >> 4);
+        if (kc < a.n_kc) {
+            float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + (lane & 15);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    g[((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2)] =
+                        make_float4(acc[0][j][i].x, acc[0][j][i].y, acc[NF - 1][j][i].x, acc[NF - 1][j][i].y);
+        }
+    } else {
+        float2 *g = a.G + (long long)kg * a.mry * a.mrx * kKC + lane;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC] = acc[0][j][i];
+    }
+}
+
+cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s) {
+    char *w = reinterpret_cast<char *>(ws);
+    SpreadGroupArgs a;
+    a.shat = reinterpret_cast<const float2 *>(w + p.off_shat);
+    a.gdd = reinterpret_cast<const int2 *>(w + p.off_gdd);
+    a.gxq = reinterpret_cast<const float4 *>(w + p.off_gxq);
+    a.yq = reinterpret_cast<const float4 *>(w + p.off_yq);
+    a.goff = reinterpret_cast<const int4 *>(w + p.off_goff);
+    a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
+    a.cls = reinterpret_cast<const int *>(w + p.off_cls);
+    a.G = reinterpret_cast<float2 *>(w + p.off_G);
+    a.hdr = reinterpret_cast<const WsHeader *>(w);
+    a.Lmax = p.L;
+    a.P = p.shape.n_pos;
+    a.TR = p.shape.n_tx * p.shape.n_rx;
+    a.mrx = p.mrx;
+    a.mry = p.mry;
+    a.nbx = p.nbx;
+    a.nby = p.nby;
+    a.w = p.w;
+    a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
+    a.n_kc = p.n_kc;
+    const int nf = p.spread_nf, warps = p.spread_warps;
+    const unsigned tiles = (unsigned)((p.mrx / (2 * warps)) * (p.mry / 8));
+    const unsigned blocks = tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
+    if (nf == 2 && warps == 8)
+        spread_groups_kernel<2, 8, 2, 2><<<blocks, 256, 0, s>>>(a);
+    else if (nf == 2)
+        spread_groups_kernel<2, 4, 2, 4><<<blocks, 128, 0, s>>>(a);
+    else if (warps == 8)
+        spread_groups_kernel<1, 8, 3, 2><<<blocks, 256, 0, s>>>(a);
+    else
+        spread_groups_kernel<1, 4, 3, 4><<<blocks, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mmsar

@@ -1,9 +1,10 @@
 """Autotuner of the gridding launch shape.
 
-Every shape of ``mmsar_tiles`` computes the same image; which is fastest
-depends on the scan (a small scan fills the GPU better with CTAs over 32
-frequencies or 8 x 8-cell tiles, a large one prefers 64 frequencies and
-16 x 8 cells).  ``autotune`` images the caller's own data with each shape on
+Every shape of ``mmsar_tiles`` computes the same image (the grouped form to
+rounding); which is fastest depends on the scan (a small scan fills the GPU
+better with CTAs over 32 frequencies or 8 x 8-cell tiles, a large one
+prefers 64 frequencies; arrays whose pairs share x offsets gain from the
+grouped form).  ``autotune`` images the caller's own data with each shape on
 the caller's stream, timed with CUDA events, and leaves the plan set to the
 fastest; the result is kept on the plan, so plans shared by scans of one
 shape are tuned once.  Only the plan's launch shape changes: the kernels
@@ -11,18 +12,24 @@ and the images are the library's.
 """
 from __future__ import annotations
 
-SHAPES = ((2, 8), (1, 8), (2, 4), (1, 4))   # (frequencies per lane, warps per CTA)
+# (frequencies per lane, warps per CTA, grouped)
+SHAPES = tuple((nf, wp, gr) for gr in (1, 0) for nf, wp in ((2, 8), (1, 8), (2, 4), (1, 4)))
 
 
 def autotune(plan, ws, echo, pos, tx, rx, vol, echo_scale=None, stream=None, reps: int = 3,
              shapes=SHAPES) -> dict:
     """Time ``reps`` images per launch shape (after one untimed image) and set
-    the fastest on ``plan``.  Returns {"tiles": (nf, warps), "ms": {shape: ms}}."""
+    the fastest on ``plan``.  Returns {"tiles": (nf, warps, grouped), "ms": {shape: ms}}.
+    Grouped shapes are skipped when the plan rejects them (too many Tx/Rx pairs)."""
     import torch
     st = stream or torch.cuda.current_stream(vol.device)
+    from ._lib import MmsarError
     times = {}
     for shp in shapes:
-        plan.set_tiles(*shp)
+        try:
+            plan.set_tiles(*shp)
+        except MmsarError:
+            continue
         plan.image(ws, echo, pos, tx, rx, vol, echo_scale=echo_scale, stream=st)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)

@@ -8,6 +8,7 @@ also asserts that tighter, derived bound so that a kernel slip far below the
 contract still fails.  Peak voxels must be identical unless the top two
 voxels are within 1e-3 of each other (a near tie).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -326,6 +327,41 @@ def test_gridding_launch_shapes_are_bit_identical(dev):
     ref = vols[(2, 8)]
     for shp, v in vols.items():
         assert np.array_equal(v.view(np.uint64), ref.view(np.uint64)), shp
+    assert_parity(ref, oracle_of(scan), 6)
+
+
+@pytest.mark.parametrize("layout", ["awr1443", "3x4", "tiny", "offset_x"])
+def test_grouped_gridding(dev, layout):
+    """The grouped form (the samples of a position whose pairs share x' summed
+    in y first, the x weights applied once) against the oracle, for every
+    launch shape; bit-identical among its shapes, and within rounding of the
+    per-sample form.  offset_x puts the Tx and Rx at different x offsets
+    (two pairs share one, the rest are alone): several classes per position."""
+    import synth as sy
+    scan = sy.custom(nx_pos=9, ny_pos=7, nk=40, layout="awr1443" if layout == "offset_x" else layout, nx=24, ny=20,
+                     nz=10, seed=23, jitter=(0.7e-3, 3e-3), snr_db=25)
+    if layout == "offset_x":
+        tx, rx = np.array(scan.tx, np.float64), np.array(scan.rx, np.float64)
+        tx[:, 0] = [0.0, 1.0e-3]
+        rx[:, 0] = [1.0e-3, 0.0, 0.5e-3, -0.5e-3]   # sums: Tx0+Rx0 = Tx1+Rx1 = 1 mm
+        echo = sy.echo(scan.pos, tx, rx, scan.f0, scan.df, scan.echo.shape[3], scan.scatterers)
+        scan = dataclasses.replace(scan, echo=echo, tx=tx, rx=rx)
+    from paper_2305_02064_gb300 import Plan
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    vols = {}
+    for shp in ((2, 8, 1), (1, 8, 1), (2, 4, 1), (1, 4, 1), (2, 8, 0)):
+        plan = Plan.for_scan(scan)
+        plan.set_tiles(*shp)
+        ws = plan.new_workspace(dev)
+        vol = torch.full(plan.volume_shape, complex(np.nan, np.nan), dtype=torch.complex64, device=dev)
+        plan.image(ws, t(scan.echo), t(np.asarray(scan.pos, np.float64)), t(np.asarray(scan.tx, np.float64)),
+                   t(np.asarray(scan.rx, np.float64)), vol)
+        plan.poll_error(ws)
+        vols[shp] = vol.cpu().numpy()
+    ref = vols[(2, 8, 1)]
+    for shp in ((1, 8, 1), (2, 4, 1), (1, 4, 1)):
+        assert np.array_equal(vols[shp].view(np.uint64), ref.view(np.uint64)), shp
+    assert rma.nmse(ref, vols[(2, 8, 0)]) < 1e-12
     assert_parity(ref, oracle_of(scan), 6)
 
 
