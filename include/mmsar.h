@@ -119,7 +119,7 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
  * the per-sample shapes, to rounding between the per-sample and the grouped
  * form (another summation order); they differ in speed, which depends on the
  * scan (small scans fill the GPU better with smaller CTAs; arrays whose Tx
- * and Rx lie on one line along y give large groups).  Defaults: 2, 8, 0. */
+ * and Rx lie on one line along y give large groups).  Defaults: 2, 4, 0. */
 typedef struct {
     int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64           */
     int grid_warps_per_cta;    /* 4: an 8 x 8-cell tile; 8: a 16 x 8-cell tile     */

@@ -130,7 +130,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.nby = p.mry / kBin;
     p.n_bins = (int64_t)p.nbx * p.nby;
     p.spread_nf = 2;
-    p.spread_warps = 8;
+    p.spread_warps = 4;   // the autotuner's choice on the realistic, large and most batched scans
     p.grouped = false;
     p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
