@@ -198,6 +198,18 @@ typedef struct {
  * enqueued). */
 mmsar_status mmsar_image_batch(const mmsar_request *reqs, int n, void *const *streams, int n_streams);
 
+/* The same n images (Sec. III imaging of several independent scans) as
+ * fused launches on one stream: every stage of mmsar_image runs as one
+ * launch for all requests that use the same kernel instance (up to 32 scans
+ * per launch; requests of other FFT lengths, gridding shapes, echo types or
+ * Stolt grids form further launches), so an uneven batch fills the GPU with
+ * a handful of launches instead of ten per scan.  Each request needs its own
+ * workspace; the images are bit for bit those of mmsar_image.  `launches`
+ * (may be NULL) receives the number of kernels enqueued.  Returns the first
+ * validation or launch error (nothing is enqueued after a validation error
+ * of any request). */
+mmsar_status mmsar_image_batch_fused(const mmsar_request *reqs, int n, void *stream, int *launches);
+
 /* Read (and clear) the device error word of the last call that used this
  * workspace: synchronises `stream`, returns MMSAR_OK or the first device-side
  * condition (MMSAR_ERR_NONFINITE, MMSAR_ERR_INVALID_ARG for Z_c <= 0). */

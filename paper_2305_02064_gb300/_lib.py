@@ -27,8 +27,8 @@ EXPORTS = ["mmsar_options_default", "mmsar_plan_create", "mmsar_plan_workspace_b
            "mmsar_stage_count", "mmsar_stage_name", "mmsar_plan_set_stage_events",
            "mmsar_image", "mmsar_poll_error", "mmsar_peak_scratch_bytes", "mmsar_peak", "mmsar_last_error",
            "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static",
-           "mmsar_quantize_echo", "mmsar_image_batch", "mmsar_backproject", "mmsar_plan_set_tiles",
-           "mmsar_plan_get_tiles"]
+           "mmsar_quantize_echo", "mmsar_image_batch", "mmsar_image_batch_fused", "mmsar_backproject",
+           "mmsar_plan_set_tiles", "mmsar_plan_get_tiles"]
 
 
 class MmsarError(RuntimeError):
@@ -117,6 +117,9 @@ def load(build_if_missing: bool = True):
         lib.mmsar_quantize_echo.restype = ctypes.c_int
         lib.mmsar_image_batch.argtypes = [ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int]
         lib.mmsar_image_batch.restype = ctypes.c_int
+        lib.mmsar_image_batch_fused.argtypes = [ctypes.POINTER(Request), ctypes.c_int, vp,
+                                                ctypes.POINTER(ctypes.c_int)]
+        lib.mmsar_image_batch_fused.restype = ctypes.c_int
         lib.mmsar_backproject.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp]
         lib.mmsar_backproject.restype = ctypes.c_int
         lib.mmsar_plan_set_tiles.argtypes = [vp, ctypes.POINTER(Tiles)]

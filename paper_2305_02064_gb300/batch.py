@@ -4,8 +4,10 @@ Each scan becomes a ``ScanJob``: its plan, its echo/geometry resident on the
 device (optionally stored as FP16/BF16 with a per-scan scale), a private
 workspace and an output volume.  ``image_batch`` enqueues all jobs through
 ``mmsar_image_batch`` round-robin over several CUDA streams so that small
-scans overlap on the GPU; ``BatchGraph`` captures such a batch once into a CUDA
-graph and replays it with a single launch.  Every kernel that runs is the
+scans overlap on the GPU; ``image_batch_fused`` enqueues them through
+``mmsar_image_batch_fused`` instead, one launch per stage and kernel shape for
+the whole batch; ``BatchGraph`` captures either form once into a CUDA graph
+and replays it with a single launch.  Every kernel that runs is the
 library's; this module only marshals pointers and streams.
 """
 from __future__ import annotations
@@ -85,16 +87,34 @@ def image_batch(jobs, streams):
     _lib.check(lib.mmsar_image_batch(reqs, len(jobs), hs, len(streams)))
 
 
-class BatchGraph:
-    """A fixed batch captured once into a CUDA graph (fork onto n_streams
-    streams, image every job, join) and replayed with one launch."""
+def image_batch_fused(jobs, stream=None) -> int:
+    """Enqueue every job through mmsar_image_batch_fused on one stream (one
+    launch per stage and kernel shape); returns the kernels enqueued."""
+    import torch
+    lib = _lib.load()
+    reqs = (_lib.Request * len(jobs))(*[j.request() for j in jobs])
+    s = stream or torch.cuda.current_stream()
+    n = ctypes.c_int()
+    _lib.check(lib.mmsar_image_batch_fused(reqs, len(jobs), ctypes.c_void_p(s.cuda_stream), ctypes.byref(n)))
+    return n.value
 
-    def __init__(self, jobs, n_streams=4, device=None):
+
+class BatchGraph:
+    """A fixed batch captured once into a CUDA graph and replayed with one
+    launch: forked onto n_streams streams, either ten launches per job
+    (round-robin), or with ``fused`` the jobs split round-robin into
+    n_streams sub-batches, each as the fused launches of
+    mmsar_image_batch_fused on its own stream (so the stages of different
+    sub-batches overlap)."""
+
+    def __init__(self, jobs, n_streams=4, device=None, fused=False):
         import torch
         self.jobs = list(jobs)
+        self.fused = fused
         dev = device or self.jobs[0].vol.device
         self.main = torch.cuda.Stream(device=dev)
         self.side = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+        self.launches = 0
         # one eager pass first (kernel attributes are set outside the capture)
         self._enqueue()
         torch.cuda.synchronize(dev)
@@ -107,7 +127,13 @@ class BatchGraph:
         cur = torch.cuda.current_stream()
         for s in self.side:
             s.wait_stream(cur)
-        image_batch(self.jobs, self.side)
+        if self.fused:
+            k = len(self.side)
+            self.launches = sum(image_batch_fused(self.jobs[i::k], self.side[i]) for i in range(k)
+                                if self.jobs[i::k])
+        else:
+            image_batch(self.jobs, self.side)
+            self.launches = sum(j.plan.kernels_per_image for j in self.jobs)
         for s in self.side:
             cur.wait_stream(s)
 

@@ -39,7 +39,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // selected rows are scaled and stored.  VEC complex values per copy (2 when
 // every row start is 16-byte aligned, else 1).
 template <int L, int SIGN, int VEC>
-__global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
+__device__ __forceinline__ void column_fft_body(const ColumnFFT &a, int bx, int by) {
     constexpr int C = fft_cols(L);
     constexpr int P = fft_tile_pitch(C);
     extern __shared__ __align__(16) float2 smem[];
@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(ColumnFFT a) {
     float2 *tw = smem + L * P;
     const int tid = threadIdx.x;
     const int nchunks = (a.ncols + C - 1) / C;
-    const int chunk = blockIdx.x % nchunks;
-    const int t2 = blockIdx.x / nchunks;
-    const int t1 = blockIdx.y;
+    const int chunk = bx % nchunks;
+    const int t2 = bx / nchunks;
+    const int t1 = by;
     if (a.tile_win) {
         const int len = a.tile_win[1];
         if (len < a.nt2) {
@@ -108,7 +108,7 @@ __host__ __device__ constexpr int reg_fft_pitch(int L) {
 }
 
 template <int L, int SIGN>
-__global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a) {
+__device__ __forceinline__ void column_fft_reg_body(const ColumnFFT &a, int bx, int by) {
     constexpr int N1 = reg_fft_n1(L), N2 = L / N1;
     constexpr int C = fft_cols(L);
     constexpr int IT1 = N2 * C / kFftThreads;   // step-1 columns per thread (N1 values each)
@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
     float *dscale = reinterpret_cast<float *>(tw + L);   // [n_out <= L]: output row scales
     const int tid = threadIdx.x;
     const int nchunks = (a.ncols + C - 1) / C;
-    const int chunk = blockIdx.x % nchunks;
-    const int t2 = blockIdx.x / nchunks;
-    const int t1 = blockIdx.y;
+    const int chunk = bx % nchunks;
+    const int t2 = bx / nchunks;
+    const int t1 = by;
     if (a.tile_win) {
         const int len = a.tile_win[1];
         if (len < a.nt2) {
@@ -202,61 +202,128 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_reg_kernel(ColumnFFT a
     }
 }
 
-template <int L, int SIGN>
-static cudaError_t launch_reg(const ColumnFFT &a, cudaStream_t s) {
-    constexpr int C = fft_cols(L);
-    const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2) + L * sizeof(float);
-    cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN>, smem);
-    if (e != cudaSuccess) return e;
-    const int nchunks = (a.ncols + C - 1) / C;
-    dim3 grid((unsigned)(a.nt2 * nchunks), (unsigned)a.nt1);
-    column_fft_reg_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 template <int L, int SIGN, int VEC>
-static cudaError_t launch_LV(const ColumnFFT &a, cudaStream_t s) {
-    constexpr int C = fft_cols(L);
-    const size_t smem = (size_t)(L * fft_tile_pitch(C) + L) * sizeof(float2);
-    cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN, VEC>, smem);
-    if (e != cudaSuccess) return e;
-    const int nchunks = (a.ncols + C - 1) / C;
-    dim3 grid((unsigned)(a.nt2 * nchunks), (unsigned)a.nt1);
-    column_fft_kernel<L, SIGN, VEC><<<grid, kFftThreads, smem, s>>>(a);
-    return cudaGetLastError();
+__global__ void __launch_bounds__(kFftThreads) column_fft_kernel(const __grid_constant__ ColumnFFT a) {
+    column_fft_body<L, SIGN, VEC>(a, blockIdx.x, blockIdx.y);
+}
+// three CTAs per SM, as the tiles' shared memory allows
+template <int L, int SIGN>
+__global__ void __launch_bounds__(kFftThreads, 3)
+    column_fft_reg_kernel(const __grid_constant__ ColumnFFT a) {
+    column_fft_reg_body<L, SIGN>(a, blockIdx.x, blockIdx.y);
 }
 
+// Fused launches: the tiles of every scan on a 1-D grid (x fastest as above).
+template <int L, int SIGN, int VEC>
+__global__ void __launch_bounds__(kFftThreads)
+    column_fft_multi(const __grid_constant__ BatchTable<ColumnFFT> t) {
+    __shared__ ColumnFFT sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    const int gx = sa.nt2 * ((sa.ncols + fft_cols(L) - 1) / fft_cols(L));
+    column_fft_body<L, SIGN, VEC>(sa, bid % gx, bid / gx);
+}
 template <int L, int SIGN>
-static cudaError_t launch_L(const ColumnFFT &a, cudaStream_t s) {
+__global__ void __launch_bounds__(kFftThreads, 3)
+    column_fft_reg_multi(const __grid_constant__ BatchTable<ColumnFFT> t) {
+    __shared__ ColumnFFT sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    const int gx = sa.nt2 * ((sa.ncols + fft_cols(L) - 1) / fft_cols(L));
+    column_fft_reg_body<L, SIGN>(sa, bid % gx, bid / gx);
+}
+
+// Kernel instance of a transform: bit 0-1 the kind (0 register kernel,
+// 1 / 2 the shared-memory kernel with 8- / 16-byte copies), bits 2.. L,
+// bit 20 the inverse sign.
+static int fft_key(const ColumnFFT &a) {
+    const bool reg = a.n_in == a.L && a.L >= 64 && a.L <= 1024;
     // 16-byte copies need every row start (and the column chunk starts) on a
     // 16-byte boundary
     const bool even = (a.ncols % 2 == 0) && (a.in_row % 2 == 0) && (a.in_t1 % 2 == 0) && (a.in_t2 % 2 == 0) &&
                       (reinterpret_cast<uintptr_t>(a.in) % 16 == 0);
-    return even ? launch_LV<L, SIGN, 2>(a, s) : launch_LV<L, SIGN, 1>(a, s);
+    return (a.sign > 0 ? 1 << 20 : 0) | (a.L << 2) | (reg ? 0 : (even ? 2 : 1));
+}
+
+static int fft_blocks(const ColumnFFT &a) {
+    if (a.nt1 <= 0 || a.nt2 <= 0 || a.ncols <= 0) return 0;
+    const int C = fft_cols(a.L);
+    return a.nt1 * a.nt2 * ((a.ncols + C - 1) / C);
+}
+
+template <int L, int SIGN>
+static cudaError_t launch_reg(const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks, cudaStream_t s) {
+    constexpr int C = fft_cols(L);
+    const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2) + L * sizeof(float);
+    if (a) {
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN>, smem);
+        if (e != cudaSuccess) return e;
+        const int nchunks = (a->ncols + C - 1) / C;
+        dim3 grid((unsigned)(a->nt2 * nchunks), (unsigned)a->nt1);
+        column_fft_reg_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(*a);
+    } else {
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_multi<L, SIGN>, smem);
+        if (e != cudaSuccess) return e;
+        column_fft_reg_multi<L, SIGN><<<blocks, kFftThreads, smem, s>>>(*t);
+    }
+    return cudaGetLastError();
+}
+
+template <int L, int SIGN, int VEC>
+static cudaError_t launch_LV(const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks, cudaStream_t s) {
+    constexpr int C = fft_cols(L);
+    const size_t smem = (size_t)(L * fft_tile_pitch(C) + L) * sizeof(float2);
+    if (a) {
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_kernel<L, SIGN, VEC>, smem);
+        if (e != cudaSuccess) return e;
+        const int nchunks = (a->ncols + C - 1) / C;
+        dim3 grid((unsigned)(a->nt2 * nchunks), (unsigned)a->nt1);
+        column_fft_kernel<L, SIGN, VEC><<<grid, kFftThreads, smem, s>>>(*a);
+    } else {
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_multi<L, SIGN, VEC>, smem);
+        if (e != cudaSuccess) return e;
+        column_fft_multi<L, SIGN, VEC><<<blocks, kFftThreads, smem, s>>>(*t);
+    }
+    return cudaGetLastError();
+}
+
+template <int L, int SIGN>
+static cudaError_t launch_kind(int kind, const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks,
+                               cudaStream_t s) {
+    if constexpr (L >= 64 && L <= 1024)
+        if (kind == 0) return launch_reg<L, SIGN>(a, t, blocks, s);
+    return kind == 2 ? launch_LV<L, SIGN, 2>(a, t, blocks, s) : launch_LV<L, SIGN, 1>(a, t, blocks, s);
 }
 
 template <int SIGN>
-static cudaError_t dispatch(const ColumnFFT &a, cudaStream_t s) {
-    switch (a.L) {
-        case 16: return launch_L<16, SIGN>(a, s);
-        case 32: return launch_L<32, SIGN>(a, s);
-        case 64: return a.n_in == 64 ? launch_reg<64, SIGN>(a, s) : launch_L<64, SIGN>(a, s);
-        case 128: return a.n_in == 128 ? launch_reg<128, SIGN>(a, s) : launch_L<128, SIGN>(a, s);
-        case 256: return a.n_in == 256 ? launch_reg<256, SIGN>(a, s) : launch_L<256, SIGN>(a, s);
-        case 512: return a.n_in == 512 ? launch_reg<512, SIGN>(a, s) : launch_L<512, SIGN>(a, s);
-        case 1024: return a.n_in == 1024 ? launch_reg<1024, SIGN>(a, s) : launch_L<1024, SIGN>(a, s);
-        case 2048: return launch_L<2048, SIGN>(a, s);
+static cudaError_t dispatch(int L, int kind, const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks,
+                            cudaStream_t s) {
+    switch (L) {
+        case 16: return launch_kind<16, SIGN>(kind, a, t, blocks, s);
+        case 32: return launch_kind<32, SIGN>(kind, a, t, blocks, s);
+        case 64: return launch_kind<64, SIGN>(kind, a, t, blocks, s);
+        case 128: return launch_kind<128, SIGN>(kind, a, t, blocks, s);
+        case 256: return launch_kind<256, SIGN>(kind, a, t, blocks, s);
+        case 512: return launch_kind<512, SIGN>(kind, a, t, blocks, s);
+        case 1024: return launch_kind<1024, SIGN>(kind, a, t, blocks, s);
+        case 2048: return launch_kind<2048, SIGN>(kind, a, t, blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
+static cudaError_t launch_key(int key, const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks,
+                              cudaStream_t s) {
+    const int L = (key >> 2) & 0x3ffff, kind = key & 3;
+    return (key >> 20) ? dispatch<+1>(L, kind, a, t, blocks, s) : dispatch<-1>(L, kind, a, t, blocks, s);
+}
+
 cudaError_t launch_column_fft(const ColumnFFT &a, cudaStream_t s) {
-    if (a.nt1 <= 0 || a.nt2 <= 0 || a.ncols <= 0) return cudaSuccess;
-    return a.sign < 0 ? dispatch<-1>(a, s) : dispatch<+1>(a, s);
+    if (fft_blocks(a) == 0) return cudaSuccess;
+    return launch_key(fft_key(a), &a, nullptr, 0, s);
 }
 
 // ---------------------------------------------------------------- FT_2D
-cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s) {
+static ColumnFFT fft_x_args(const Plan &p, void *ws) {
     char *w = reinterpret_cast<char *>(ws);
     const float2 *G = reinterpret_cast<const float2 *>(w + p.off_G);
     float2 *A = reinterpret_cast<float2 *>(w + p.off_A);
@@ -283,10 +350,10 @@ cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s) {
     const WsHeader *hdr = reinterpret_cast<const WsHeader *>(w);
     u.in_win = &hdr->u_lo;     // cells of a row outside the occupied window are zero
     u.tile_win = &hdr->v_lo;   // rows outside it are zero: skipped, A left unwritten
-    return launch_column_fft(u, s);
+    return u;
 }
 
-cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s) {
+static ColumnFFT fft_y_args(const Plan &p, void *ws) {
     char *w = reinterpret_cast<char *>(ws);
     const float2 *A = reinterpret_cast<const float2 *>(w + p.off_A);
     float2 *S = reinterpret_cast<float2 *>(w + p.off_S);
@@ -312,11 +379,11 @@ cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s) {
     v.gauss_tau = (float)p.tau_y;
     v.in_win = &reinterpret_cast<const WsHeader *>(w)->v_lo;   // only the occupied rows of A
     v.tile_win = nullptr;
-    return launch_column_fft(v, s);
+    return v;
 }
 
 // ---------------------------------------------------------------- IFT over (k_x, k_y)
-cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s) {
+static ColumnFFT ifft_y_args(const Plan &p, void *ws) {
     char *w = reinterpret_cast<char *>(ws);
     const float2 *Z = reinterpret_cast<const float2 *>(w + p.off_Z);
     float2 *B = reinterpret_cast<float2 *>(w + p.off_B);
@@ -343,10 +410,10 @@ cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s) {
     a.gauss_tau = 0.f;
     a.in_win = nullptr;
     a.tile_win = nullptr;
-    return launch_column_fft(a, s);
+    return a;
 }
 
-cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s) {
+static ColumnFFT ifft_x_args(const Plan &p, void *ws, void *vol) {
     char *w = reinterpret_cast<char *>(ws);
     const float2 *B = reinterpret_cast<const float2 *>(w + p.off_B);
     const int nx = p.grid.nx, ny = p.grid.ny, nz = p.grid.nz;
@@ -372,7 +439,34 @@ cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s) {
     b.gauss_tau = 0.f;
     b.in_win = nullptr;
     b.tile_win = nullptr;
-    return launch_column_fft(b, s);
+    return b;
+}
+
+cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s) { return launch_column_fft(fft_x_args(p, ws), s); }
+cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s) { return launch_column_fft(fft_y_args(p, ws), s); }
+cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s) { return launch_column_fft(ifft_y_args(p, ws), s); }
+cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s) {
+    return launch_column_fft(ifft_x_args(p, ws, vol), s);
+}
+
+// stage 0: along x', 1: along y', 2: inverse along k_y, 3: inverse along k_x
+cudaError_t launch_fft_multi(const mmsar_request *r, int n, int stage, cudaStream_t s) {
+    std::vector<ColumnFFT> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const Plan &p = r[i].plan->p;
+        void *ws = r[i].workspace;
+        args[i] = stage == 0 ? fft_x_args(p, ws)
+                  : stage == 1 ? fft_y_args(p, ws)
+                  : stage == 2 ? ifft_y_args(p, ws)
+                               : ifft_x_args(p, ws, r[i].vol);
+        blocks[i] = fft_blocks(args[i]);
+        keys[i] = fft_key(args[i]);
+    }
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int key, const BatchTable<ColumnFFT> &t, int total) {
+                             return launch_key(key, nullptr, &t, total, s);
+                         });
 }
 
 }  // namespace mmsar

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mmsar.h"
 
 namespace mmsar {
@@ -129,6 +131,97 @@ cudaError_t launch_ifft_y(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_ifft_x(const Plan &p, void *ws, void *vol, cudaStream_t s);
 cudaError_t launch_peak(const void *vol, int64_t n, void *scratch, void *result, cudaStream_t s);
 size_t peak_scratch_bytes(int64_t n);
+
+// ---------------------------------------------------------------- fused batches
+// A fused launch runs one stage for up to kBatchMax scans that use the same
+// kernel instance: the blocks of scan i are blocks start[i] .. start[i+1]-1
+// of the launch, and the scans' arguments travel in one kernel parameter
+// block (__grid_constant__, a few KB).
+constexpr int kBatchMax = 32;
+
+template <typename A>
+struct BatchTable {
+    A a[kBatchMax];
+    int start[kBatchMax + 1];
+    int n;
+};
+
+// The scan of this block of a fused launch (binary search over the block
+// starts), the block's index inside that scan and the scan's block count.
+template <typename A>
+__device__ __forceinline__ int batch_scan(const BatchTable<A> &t, int &bid, int &nb) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = t.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (t.start[mid] <= b) lo = mid; else hi = mid;
+    }
+    bid = b - t.start[lo];
+    nb = t.start[lo + 1] - t.start[lo];
+    return lo;
+}
+
+// Copy the block's scan arguments to shared memory once (every thread calls
+// it; the copy is visible after it returns), so that the kernel body reads
+// them with plain shared-memory loads.
+template <typename A>
+__device__ __forceinline__ void batch_args(const BatchTable<A> &t, int s, A *dst) {
+    static_assert(sizeof(A) % 4 == 0, "argument block of whole words");
+    const int *src = reinterpret_cast<const int *>(&t.a[s]);
+    int *d = reinterpret_cast<int *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) d[i] = src[i];
+    __syncthreads();
+}
+
+// Host side: launch fn(key, table, blocks) once per group of scans with the
+// same key (in order of first appearance), in chunks of kBatchMax.
+// kernels the fused launches of the current batch call have made (host)
+inline thread_local int g_fused_launches = 0;
+
+template <typename A, typename K, typename F>
+cudaError_t launch_groups(int n, const K *keys, const A *args, const int *blocks, F fn) {
+    std::vector<char> done((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (done[i] || blocks[i] <= 0) continue;
+        BatchTable<A> t;
+        t.n = 0;
+        int total = 0;
+        for (int j = i; j < n; ++j) {
+            if (done[j] || blocks[j] <= 0 || !(keys[j] == keys[i])) continue;
+            done[j] = 1;
+            t.a[t.n] = args[j];
+            t.start[t.n] = total;
+            total += blocks[j];
+            ++t.n;
+            if (t.n == kBatchMax) {
+                t.start[t.n] = total;
+                const cudaError_t e = fn(keys[i], t, total);
+                if (e != cudaSuccess) return e;
+                ++g_fused_launches;
+                t.n = 0;
+                total = 0;
+            }
+        }
+        if (t.n > 0) {
+            t.start[t.n] = total;
+            const cudaError_t e = fn(keys[i], t, total);
+            if (e != cudaSuccess) return e;
+            ++g_fused_launches;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Fused launches of the stages of mmsar_image for n requests (same order and
+// meaning as the single-scan launchers; requests without samples excluded).
+cudaError_t launch_clear_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_zref_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_geometry_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_bin_scatter_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_compensate_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_spread_multi(const mmsar_request *r, int n, cudaStream_t s);
+cudaError_t launch_fft_multi(const mmsar_request *r, int n, int stage, cudaStream_t s);   // stage 0..3: x, y, iy, ix
+cudaError_t launch_stolt_multi(const mmsar_request *r, int n, cudaStream_t s);
 
 // Record a formatted message for mmsar_last_error() and return `st`.
 mmsar_status report_error(mmsar_status st, const char *fmt, ...);

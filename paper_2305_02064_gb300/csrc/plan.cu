@@ -54,6 +54,40 @@ static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 static const double kGaussErr[13] = {0, 0, 0, 0, 4.8e-3, 1.4e-3, 5.5e-4, 1.5e-4, 5.4e-5, 1.6e-5, 4.4e-6,
                                      1.3e-6, 3.5e-7};
 
+// ------------------------------------------------------------------ fused header clear
+// The region of each workspace that a new image must find zero (header,
+// z_ref partial sums, bin counts): 16-byte stores.
+struct ClearArgs {
+    int4 *p;
+    long long n16;
+};
+
+__global__ void __launch_bounds__(256) clear_multi(const __grid_constant__ BatchTable<ClearArgs> t) {
+    int bid, nb;
+    const ClearArgs &c = t.a[batch_scan(t, bid, nb)];
+    int4 *p = c.p;
+    const long long n16 = c.n16;
+    for (long long i = (long long)bid * 256 + threadIdx.x; i < n16; i += (long long)nb * 256)
+        p[i] = make_int4(0, 0, 0, 0);
+}
+
+cudaError_t launch_clear_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<ClearArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n, 0);
+    for (int i = 0; i < n; ++i) {
+        const Plan &p = r[i].plan->p;
+        const size_t bytes = p.off_counts + sizeof(int) * (size_t)p.n_bins;   // a multiple of 16
+        args[i].p = reinterpret_cast<int4 *>(r[i].workspace);
+        args[i].n16 = (long long)(bytes / 16);
+        blocks[i] = (int)std::min<long long>((args[i].n16 + 1023) / 1024, 1024);
+    }
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int, const BatchTable<ClearArgs> &t, int total) {
+                             clear_multi<<<total, 256, 0, s>>>(t);
+                             return cudaGetLastError();
+                         });
+}
+
 static int width_for_tol(double tol) {
     for (int w = 4; w <= 12; ++w)
         if (kGaussErr[w] <= tol) return w;
@@ -280,9 +314,10 @@ mmsar_status mmsar_plan_set_stage_events(mmsar_plan *plan, void *const *events, 
     return MMSAR_OK;
 }
 
-mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_bytes, const void *echo,
-                         const float *echo_scale, const double *pos, const double *tx, const double *rx, void *vol,
-                         void *stream) {
+// The argument checks of one image (shared by the single and batched calls).
+static mmsar_status check_request(const mmsar_plan *plan, const void *workspace, size_t workspace_bytes,
+                                  const void *echo, const float *echo_scale, const double *pos, const double *tx,
+                                  const double *rx, const void *vol) {
     if (!plan) return fail(MMSAR_ERR_INVALID_ARG, "null plan");
     const Plan &p = plan->p;
     if (!workspace || !vol) return fail(MMSAR_ERR_INVALID_ARG, "null workspace or output volume");
@@ -295,6 +330,15 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     if (p.L > 0 && (!echo || !pos || !tx || !rx)) return fail(MMSAR_ERR_INVALID_ARG, "null input pointer");
     if (p.L > 0 && p.shape.dtype != MMSAR_ECHO_C64 && !echo_scale)
         return fail(MMSAR_ERR_INVALID_ARG, "scaled FP16/BF16 echo needs echo_scale");
+    return MMSAR_OK;
+}
+
+mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_bytes, const void *echo,
+                         const float *echo_scale, const double *pos, const double *tx, const double *rx, void *vol,
+                         void *stream) {
+    const mmsar_status st = check_request(plan, workspace, workspace_bytes, echo, echo_scale, pos, tx, rx, vol);
+    if (st != MMSAR_OK) return st;
+    const Plan &p = plan->p;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t vol_bytes = sizeof(float2) * (size_t)p.grid.nx * p.grid.ny * p.grid.nz;
     cudaError_t e = cudaMemsetAsync(workspace, 0, p.off_counts + sizeof(int) * (size_t)p.n_bins, s);
@@ -343,6 +387,59 @@ mmsar_status mmsar_image_batch(const mmsar_request *reqs, int n, void *const *st
                                             r.rx, r.vol, streams[i % n_streams]);
         if (st != MMSAR_OK) return st;
     }
+    return MMSAR_OK;
+}
+
+mmsar_status mmsar_image_batch_fused(const mmsar_request *reqs, int n, void *stream, int *launches) {
+    if (launches) *launches = 0;
+    if (n < 0 || (n > 0 && !reqs)) return fail(MMSAR_ERR_INVALID_ARG, "bad arguments to mmsar_image_batch_fused");
+    std::vector<mmsar_request> live;
+    live.reserve((size_t)n);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n; ++i) {
+        const mmsar_request &r = reqs[i];
+        const mmsar_status st =
+            check_request(r.plan, r.workspace, r.workspace_bytes, r.echo, r.echo_scale, r.pos, r.tx, r.rx, r.vol);
+        if (st != MMSAR_OK) return st;
+    }
+    int count = 0;
+    for (int i = 0; i < n; ++i) {
+        const mmsar_request &r = reqs[i];
+        const Plan &p = r.plan->p;
+        if (p.L > 0) {
+            live.push_back(r);
+        } else {   // no samples: the volume is zero
+            const size_t vol_bytes = sizeof(float2) * (size_t)p.grid.nx * p.grid.ny * p.grid.nz;
+            const cudaError_t e = cudaMemsetAsync(r.vol, 0, vol_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e, "clearing a volume");
+            ++count;
+        }
+    }
+    const int m = (int)live.size();
+    if (m == 0) {
+        if (launches) *launches = count;
+        return MMSAR_OK;
+    }
+    const mmsar_request *r = live.data();
+    g_fused_launches = 0;
+#define MMSAR_STEP(call, what)                             \
+    do {                                                   \
+        cudaError_t ee = (call);                           \
+        if (ee != cudaSuccess) return cuda_fail(ee, what); \
+    } while (0)
+    MMSAR_STEP(launch_clear_multi(r, m, s), "clearing the workspace headers");
+    MMSAR_STEP(launch_zref_multi(r, m, s), "z_ref");
+    MMSAR_STEP(launch_geometry_multi(r, m, s), "geometry");
+    MMSAR_STEP(launch_bin_scatter_multi(r, m, s), "bin scatter");
+    MMSAR_STEP(launch_compensate_multi(r, m, s), "compensation, bin sort and gridding weights");
+    MMSAR_STEP(launch_spread_multi(r, m, s), "gridding");
+    MMSAR_STEP(launch_fft_multi(r, m, 0, s), "FT_2D along x'");
+    MMSAR_STEP(launch_fft_multi(r, m, 1, s), "FT_2D along y'");
+    MMSAR_STEP(launch_stolt_multi(r, m, s), "Stolt");
+    MMSAR_STEP(launch_fft_multi(r, m, 2, s), "IFT along k_y");
+    MMSAR_STEP(launch_fft_multi(r, m, 3, s), "IFT along k_x");
+#undef MMSAR_STEP
+    if (launches) *launches = count + g_fused_launches;
     return MMSAR_OK;
 }
 

@@ -104,27 +104,34 @@ __device__ void pair_classes(const double *__restrict__ tx, const double *__rest
     }
 }
 
-__global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__restrict__ pos, int P,
-                                                            const double *__restrict__ tx, int T,
-                                                            const double *__restrict__ rx, int R, int given,
-                                                            double z_given, double z_scene, int compensate,
-                                                            double *partials, int *cls, WsHeader *hdr) {
+struct ZrefArgs {
+    const double *pos, *tx, *rx;
+    int P, T, R, given, compensate, pad;
+    double z_given, z_scene;
+    double *partials;
+    int *cls;
+    WsHeader *hdr;
+};
+
+// bid / nb: this block's index and the block count of this scan
+__device__ __forceinline__ void zref_body(const ZrefArgs &a, int bid, int nb) {
     __shared__ double red[kZrefThreads];
     __shared__ bool last;
     const int tid = threadIdx.x;
-    if (blockIdx.x == 0) {
+    const int P = a.P;
+    if (bid == 0) {
         if (tid == 0) {
-            hdr->u_min = hdr->v_min = 0x7fffffff;
-            hdr->u_max = hdr->v_max = -0x7fffffff - 1;
-            if (given) resolve_zref(z_given, z_scene, compensate, hdr);
+            a.hdr->u_min = a.hdr->v_min = 0x7fffffff;
+            a.hdr->u_max = a.hdr->v_max = -0x7fffffff - 1;
+            if (a.given) resolve_zref(a.z_given, a.z_scene, a.compensate, a.hdr);
         }
-        pair_classes(tx, rx, T, R, cls, hdr);
+        pair_classes(a.tx, a.rx, a.T, a.R, a.cls, a.hdr);
     }
-    if (given) return;
-    const int per = (P + gridDim.x - 1) / gridDim.x;
-    const int p0 = blockIdx.x * per, p1 = min(P, p0 + per);
+    if (a.given) return;
+    const int per = (P + nb - 1) / nb;
+    const int p0 = bid * per, p1 = min(P, p0 + per);
     double acc = 0.0;
-    for (int p = p0 + tid; p < p1; p += kZrefThreads) acc += pos[3 * p + 2];
+    for (int p = p0 + tid; p < p1; p += kZrefThreads) acc += a.pos[3 * p + 2];
     red[tid] = acc;
     __syncthreads();
     for (int h = kZrefThreads / 2; h > 0; h >>= 1) {
@@ -132,16 +139,16 @@ __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__rest
         __syncthreads();
     }
     if (tid == 0) {
-        partials[blockIdx.x] = red[0];
+        a.partials[bid] = red[0];
         __threadfence();
-        last = atomicAdd(&hdr->zref_done, 1) == (int)gridDim.x - 1;
+        last = atomicAdd(&a.hdr->zref_done, 1) == nb - 1;
     }
     __syncthreads();
     if (!last) return;
-    // the last block: the block sums loaded in parallel (gridDim.x <= 256),
-    // then the same fixed-order tree as above
+    // the last block: the block sums loaded in parallel (nb <= 256), then the
+    // same fixed-order tree as above
     __threadfence();
-    red[tid] = tid < (int)gridDim.x ? ((volatile double *)partials)[tid] : 0.0;
+    red[tid] = tid < nb ? ((volatile double *)a.partials)[tid] : 0.0;
     __syncthreads();
     for (int h = kZrefThreads / 2; h > 0; h >>= 1) {
         if (tid < h) red[tid] += red[tid + h];
@@ -149,25 +156,66 @@ __global__ void __launch_bounds__(kZrefThreads) zref_kernel(const double *__rest
     }
     if (tid == 0) {
         double st = 0.0, sr = 0.0;
-        for (int t = 0; t < T; ++t) st += tx[3 * t + 2];
-        for (int r = 0; r < R; ++r) sr += rx[3 * r + 2];
-        resolve_zref((P > 0 ? red[0] / P : 0.0) + 0.5 * (st / T + sr / R), z_scene, compensate, hdr);
+        for (int t = 0; t < a.T; ++t) st += a.tx[3 * t + 2];
+        for (int r = 0; r < a.R; ++r) sr += a.rx[3 * r + 2];
+        const double mean_p = P > 0 ? __ddiv_rn(red[0], (double)P) : 0.0;
+        const double mean_tr = __dmul_rn(0.5, __dadd_rn(__ddiv_rn(st, (double)a.T), __ddiv_rn(sr, (double)a.R)));
+        resolve_zref(__dadd_rn(mean_p, mean_tr), a.z_scene, a.compensate, a.hdr);
     }
+}
+
+__global__ void __launch_bounds__(kZrefThreads) zref_kernel(const __grid_constant__ ZrefArgs a) {
+    zref_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kZrefThreads) zref_multi(const __grid_constant__ BatchTable<ZrefArgs> t) {
+    __shared__ ZrefArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    zref_body(sa, bid, nb);
+}
+
+static int zref_describe(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                         ZrefArgs &a) {
+    char *w = reinterpret_cast<char *>(ws);
+    a.pos = pos;
+    a.tx = tx;
+    a.rx = rx;
+    a.P = p.shape.n_pos;
+    a.T = p.shape.n_tx;
+    a.R = p.shape.n_rx;
+    a.given = p.zref_given ? 1 : 0;
+    a.compensate = p.opt.compensate;
+    a.pad = 0;
+    a.z_given = p.z_ref;
+    a.z_scene = p.z_scene;
+    a.partials = reinterpret_cast<double *>(w + p.off_partials);
+    a.cls = reinterpret_cast<int *>(w + p.off_cls);
+    a.hdr = reinterpret_cast<WsHeader *>(w);
+    // about one position per thread, at most kZrefMaxBlocks blocks
+    int blocks = (p.shape.n_pos + kZrefThreads - 1) / kZrefThreads;
+    blocks = blocks < 1 ? 1 : (blocks > kZrefMaxBlocks ? kZrefMaxBlocks : blocks);
+    return p.zref_given ? 1 : blocks;
 }
 
 cudaError_t launch_zref(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
                         cudaStream_t s) {
-    char *w = reinterpret_cast<char *>(ws);
-    WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
-    // about one position per thread, at most kZrefMaxBlocks blocks
-    int blocks = (p.shape.n_pos + kZrefThreads - 1) / kZrefThreads;
-    blocks = blocks < 1 ? 1 : (blocks > kZrefMaxBlocks ? kZrefMaxBlocks : blocks);
-    if (p.zref_given) blocks = 1;
-    zref_kernel<<<blocks, kZrefThreads, 0, s>>>(pos, p.shape.n_pos, tx, p.shape.n_tx, rx, p.shape.n_rx,
-                                                p.zref_given ? 1 : 0, p.z_ref, p.z_scene, p.opt.compensate,
-                                                reinterpret_cast<double *>(w + p.off_partials),
-                                                reinterpret_cast<int *>(w + p.off_cls), hdr);
+    ZrefArgs a;
+    const int blocks = zref_describe(p, ws, pos, tx, rx, a);
+    zref_kernel<<<blocks, kZrefThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_zref_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<ZrefArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n, 0);
+    for (int i = 0; i < n; ++i)
+        blocks[i] = zref_describe(r[i].plan->p, r[i].workspace, r[i].pos, r[i].tx, r[i].rx, args[i]);
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int, const BatchTable<ZrefArgs> &t, int total) {
+                             zref_multi<<<total, kZrefThreads, 0, s>>>(t);
+                             return cudaGetLastError();
+                         });
 }
 
 // ------------------------------------------------------------------ geometry
@@ -229,8 +277,9 @@ __device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int 
     const double xT = px + a.tx[3 * t], yT = py + a.tx[3 * t + 1], zT = pz + a.tx[3 * t + 2];
     const double xR = px + a.rx[3 * r], yR = py + a.rx[3 * r + 1], zR = pz + a.rx[3 * r + 2];
     // Eq. 3-4: virtual element at the midpoint, separations, plane offset
-    const double xv = 0.5 * (xT + xR), yv = 0.5 * (yT + yR), zl = 0.5 * (zT + zR);
-    const double ddx = xR - xT, ddy = yR - yT;
+    const double xv = __dmul_rn(0.5, __dadd_rn(xT, xR)), yv = __dmul_rn(0.5, __dadd_rn(yT, yR));
+    const double zl = __dmul_rn(0.5, __dadd_rn(zT, zR));
+    const double ddx = __dsub_rn(xR, xT), ddy = __dsub_rn(yR, yT);
     const double z_ref = a.hdr->z_ref, inv_4zc = a.hdr->inv_4zc;
     if (!(isfinite(xv) && isfinite(yv) && isfinite(zl))) {
         atomicOr(&a.hdr->error, kErrNonfinite);
@@ -238,27 +287,37 @@ __device__ int geometry_one(const GeomArgs &a, int l, int &umin, int &umax, int 
         return -1;
     }
     // residual of the round trip over 2 R_0 (Z_c <= 0 was flagged once when
-    // z_ref was resolved; beta is then 0)
+    // z_ref was resolved; beta is then 0).  Every FP64 operation of the
+    // per-sample geometry is an explicitly rounded one (no fused
+    // multiply-adds left to the compiler), so that every kernel instance that
+    // inlines it -- one scan or a fused batch -- computes the same bits.
     double beta = 0.0;
     if (a.compensate == 1 && inv_4zc > 0.0) {
         // Eq. 12 with +z toward the scene: beta = -2 d^z + (d^x^2 + d^y^2) / (4 Z_c)
-        beta = -2.0 * (zl - z_ref) + (ddx * ddx + ddy * ddy) * inv_4zc;
+        const double d2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+        beta = __dadd_rn(__dmul_rn(-2.0, __dsub_rn(zl, z_ref)), __dmul_rn(d2, inv_4zc));
     } else if (a.compensate == 2 && inv_4zc > 0.0) {
         // Eq. 5 at the scene centre (x_c, y_c, z_ref + Z_c), Z_0 - z = -Z_c:
         //   beta = -2 Z_c d^z / R_0 + (d^x^2 + d^y^2 + 4 d^z^2) / (4 R_0)
         //          - [((x' - x_c) d^x + (y' - y_c) d^y)^2 + 4 Z_c^2 d^z^2] / (4 R_0^3)
-        const double Zc = a.hdr->zc, dz = zl - z_ref;
-        const double ax = xv - a.x_c, ay = yv - a.y_c;
-        const double R0 = sqrt(ax * ax + ay * ay + Zc * Zc);
-        const double cross = ax * ddx + ay * ddy;
-        beta = -2.0 * Zc * dz / R0 + (ddx * ddx + ddy * ddy + 4.0 * dz * dz) / (4.0 * R0) -
-               (cross * cross + 4.0 * Zc * Zc * dz * dz) / (4.0 * R0 * R0 * R0);
+        const double Zc = a.hdr->zc, dz = __dsub_rn(zl, z_ref);
+        const double ax = __dsub_rn(xv, a.x_c), ay = __dsub_rn(yv, a.y_c);
+        const double R0 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(Zc, Zc)));
+        const double cross = __dadd_rn(__dmul_rn(ax, ddx), __dmul_rn(ay, ddy));
+        const double dz2 = __dmul_rn(dz, dz);
+        const double t1 = __ddiv_rn(__dmul_rn(__dmul_rn(-2.0, Zc), dz), R0);
+        const double t2 = __ddiv_rn(
+            __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(4.0, dz2)),
+            __dmul_rn(4.0, R0));
+        const double num3 = __dadd_rn(__dmul_rn(cross, cross), __dmul_rn(__dmul_rn(4.0, __dmul_rn(Zc, Zc)), dz2));
+        const double t3 = __ddiv_rn(num3, __dmul_rn(__dmul_rn(4.0, R0), __dmul_rn(R0, R0)));
+        beta = __dsub_rn(__dadd_rn(t1, t2), t3);
     }
     // position on the 2M-point periodic grid, in cells
-    const double gx = (xv - a.x_c) * a.inv_dx2;
-    const double gy = (yv - a.y_c) * a.inv_dy2;
-    const double u0d = ceil(gx - a.half_w), v0d = ceil(gy - a.half_w);
-    const double fx = gx - u0d, fy = gy - v0d;
+    const double gx = __dmul_rn(__dsub_rn(xv, a.x_c), a.inv_dx2);
+    const double gy = __dmul_rn(__dsub_rn(yv, a.y_c), a.inv_dy2);
+    const double u0d = ceil(__dsub_rn(gx, a.half_w)), v0d = ceil(__dsub_rn(gy, a.half_w));
+    const double fx = __dsub_rn(gx, u0d), fy = __dsub_rn(gy, v0d);
     // occupied window; a sample absurdly far away (beyond 1e9 cells) makes the
     // window the whole grid
     const bool ufar = fabs(u0d) > 1.0e9, vfar = fabs(v0d) > 1.0e9;
@@ -302,14 +361,14 @@ __device__ int group_one(const GeomArgs &a, int g, int &umin, int &umax, int &vm
     const int m_beg = start[c], m_end = start[c + 1];
     const int m0 = members[m_beg], t0 = m0 / a.R, r0 = m0 - t0 * a.R;
     const double px = a.pos[3 * p], py = a.pos[3 * p + 1];
-    const double xv = 0.5 * ((px + a.tx[3 * t0]) + (px + a.rx[3 * r0]));
+    const double xv = __dmul_rn(0.5, __dadd_rn(__dadd_rn(px, a.tx[3 * t0]), __dadd_rn(px, a.rx[3 * r0])));
     bool ok = isfinite(xv);
     double vlo = 0.0, vhi = 0.0;
     for (int m = m_beg; m < m_end; ++m) {
         const int tr = members[m], t = tr / a.R, r = tr - t * a.R;
-        const double yv = 0.5 * ((py + a.tx[3 * t + 1]) + (py + a.rx[3 * r + 1]));
+        const double yv = __dmul_rn(0.5, __dadd_rn(__dadd_rn(py, a.tx[3 * t + 1]), __dadd_rn(py, a.rx[3 * r + 1])));
         ok = ok && isfinite(yv);
-        const double v0d = ceil((yv - a.y_c) * a.inv_dy2 - a.half_w);
+        const double v0d = ceil(__dsub_rn(__dmul_rn(__dsub_rn(yv, a.y_c), a.inv_dy2), a.half_w));
         vlo = m == m_beg ? v0d : fmin(vlo, v0d);
         vhi = m == m_beg ? v0d : fmax(vhi, v0d);
     }
@@ -318,8 +377,8 @@ __device__ int group_one(const GeomArgs &a, int g, int &umin, int &umax, int &vm
         a.binid[g] = -1;
         return -1;
     }
-    const double gx = (xv - a.x_c) * a.inv_dx2;
-    const double u0d = ceil(gx - a.half_w);
+    const double gx = __dmul_rn(__dsub_rn(xv, a.x_c), a.inv_dx2);
+    const double u0d = ceil(__dsub_rn(gx, a.half_w));
     const bool ufar = fabs(u0d) > 1.0e9, vfar = fabs(vlo) > 1.0e9 || fabs(vhi) > 1.0e9;
     umin = ufar ? -1073741824 : (int)u0d;
     umax = ufar ? 1073741823 : (int)u0d;
@@ -330,7 +389,7 @@ __device__ int group_one(const GeomArgs &a, int g, int &umin, int &umax, int &vm
     GroupRec gr;
     gr.u0 = (int)(u0l & (a.mrx - 1));
     gr.v0min = (int)(v0l & (a.mry - 1));
-    gr.fx = (float)(gx - u0d);
+    gr.fx = (float)__dsub_rn(gx, u0d);
     gr.vspan = vfar ? 0 : (int)fmin(vhi - vlo, (double)(a.mry - 1));
     a.grec[g] = gr;
     vspan = gr.vspan;
@@ -342,10 +401,10 @@ __device__ int group_one(const GeomArgs &a, int g, int &umin, int &umax, int &vm
 __device__ void scan_bins(const int *counts, int *__restrict__ offsets, int *__restrict__ cursor, int n,
                           WsHeader *hdr, int w, int mrx, int mry, int *warp_tot);
 
-__global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
+__device__ __forceinline__ void geometry_body(const GeomArgs &a, int bid, int nb) {
     __shared__ int warp_tot[32];
     __shared__ bool last;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = bid * blockDim.x + threadIdx.x;
     int bumin = 0x7fffffff, bumax = -0x7fffffff - 1, bvmin = 0x7fffffff, bvmax = -0x7fffffff - 1;
     int bin = -1, vspan = 0;
     if (l < a.L)
@@ -364,7 +423,7 @@ __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(&a.hdr->geom_done, 1) == (int)gridDim.x - 1;
+        last = atomicAdd(&a.hdr->geom_done, 1) == nb - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -372,10 +431,20 @@ __global__ void __launch_bounds__(256) geometry_kernel(GeomArgs a) {
     scan_bins(a.counts, a.offsets, a.cursor, a.n_bins, a.hdr, a.w, a.mrx, a.mry, warp_tot);
 }
 
-cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
-                            cudaStream_t s) {
+__global__ void __launch_bounds__(256) geometry_kernel(const __grid_constant__ GeomArgs a) {
+    geometry_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) geometry_multi(const __grid_constant__ BatchTable<GeomArgs> t) {
+    __shared__ GeomArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    geometry_body(sa, bid, nb);
+}
+
+static int geometry_describe(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                             GeomArgs &a) {
     char *w = reinterpret_cast<char *>(ws);
-    GeomArgs a;
     a.pos = pos;
     a.tx = tx;
     a.rx = rx;
@@ -408,9 +477,27 @@ cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const do
     a.cls = reinterpret_cast<const int *>(w + p.off_cls);
     a.grec = reinterpret_cast<GroupRec *>(w + p.off_grec);
     const long long threads = p.L + (p.grouped ? p.G : 0);
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    return (int)((threads + 255) / 256);
+}
+
+cudaError_t launch_geometry(const Plan &p, void *ws, const double *pos, const double *tx, const double *rx,
+                            cudaStream_t s) {
+    GeomArgs a;
+    const int blocks = geometry_describe(p, ws, pos, tx, rx, a);
     geometry_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<GeomArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n, 0);
+    for (int i = 0; i < n; ++i)
+        blocks[i] = geometry_describe(r[i].plan->p, r[i].workspace, r[i].pos, r[i].tx, r[i].rx, args[i]);
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int, const BatchTable<GeomArgs> &t, int total) {
+                             geometry_multi<<<total, 256, 0, s>>>(t);
+                             return cudaGetLastError();
+                         });
 }
 
 // ------------------------------------------------------------------ bin scan
@@ -508,27 +595,62 @@ __device__ void scan_bins(const int *counts, int *__restrict__ offsets, int *__r
 // Each sample takes a slot of its bin: the lanes of a warp that share a bin
 // reserve their slots with one atomic and take them in lane order (the
 // in-bin order is made deterministic afterwards by the in-bin sort).
-__global__ void __launch_bounds__(256) bin_scatter_kernel(int L, const int *__restrict__ binid,
-                                                          int *__restrict__ cursor, int *__restrict__ perm) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+struct ScatterArgs {
+    int L, pad;
+    const int *binid;
+    int *cursor, *perm;
+};
+
+__device__ __forceinline__ void bin_scatter_body(const ScatterArgs &a, int bid) {
+    const int l = bid * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int b = l < L ? binid[l] : -1;
+    const int b = l < a.L ? a.binid[l] : -1;
     const unsigned grp = __match_any_sync(0xffffffffu, b);
     const int leader = __ffs(grp) - 1;
     int base = 0;
-    if (b >= 0 && lane == leader) base = atomicAdd(&cursor[b], __popc(grp));
+    if (b >= 0 && lane == leader) base = atomicAdd(&a.cursor[b], __popc(grp));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (b >= 0) perm[base + __popc(grp & ((1u << lane) - 1u))] = l;
+    if (b >= 0) a.perm[base + __popc(grp & ((1u << lane) - 1u))] = l;
+}
+
+__global__ void __launch_bounds__(256) bin_scatter_kernel(const __grid_constant__ ScatterArgs a) {
+    bin_scatter_body(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) bin_scatter_multi(const __grid_constant__ BatchTable<ScatterArgs> t) {
+    __shared__ ScatterArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    bin_scatter_body(sa, bid);
+}
+
+static int bin_scatter_describe(const Plan &p, void *ws, ScatterArgs &a) {
+    char *w = reinterpret_cast<char *>(ws);
+    const long long items = p.grouped ? p.G : p.L;   // groups or samples
+    a.L = (int)items;
+    a.pad = 0;
+    a.binid = reinterpret_cast<const int *>(w + p.off_binid);
+    a.cursor = reinterpret_cast<int *>(w + p.off_cursor);
+    a.perm = reinterpret_cast<int *>(w + p.off_perm);
+    return (int)((items + 255) / 256);
 }
 
 cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s) {
-    char *w = reinterpret_cast<char *>(ws);
-    const long long items = p.grouped ? p.G : p.L;   // groups or samples
-    const unsigned blocks = (unsigned)((items + 255) / 256);
-    bin_scatter_kernel<<<blocks, 256, 0, s>>>((int)items, reinterpret_cast<int *>(w + p.off_binid),
-                                              reinterpret_cast<int *>(w + p.off_cursor),
-                                              reinterpret_cast<int *>(w + p.off_perm));
+    ScatterArgs a;
+    const int blocks = bin_scatter_describe(p, ws, a);
+    bin_scatter_kernel<<<blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<ScatterArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n, 0);
+    for (int i = 0; i < n; ++i) blocks[i] = bin_scatter_describe(r[i].plan->p, r[i].workspace, args[i]);
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int, const BatchTable<ScatterArgs> &t, int total) {
+                             bin_scatter_multi<<<total, 256, 0, s>>>(t);
+                             return cudaGetLastError();
+                         });
 }
 
 // ------------------------------------------------------------------ compensate and in-bin order
@@ -737,12 +859,12 @@ struct PrepTailArgs {
 // (one 16-byte or 8-byte load, one 16-byte store per sample; Nk even and the
 // echo aligned); otherwise 64 g + l and 64 g + 32 + l.
 template <int DT, bool VEC>
-__global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArgs a) {
+__device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) {
     __shared__ int keys[kPrepWarps][kSortBinCap];
     __shared__ int sorted[kPrepWarps][kSortBinCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if ((int)blockIdx.x < a.n_sort_blocks) {
-        const int b = blockIdx.x * kPrepWarps + warp;
+    if (bid < a.n_sort_blocks) {
+        const int b = bid * kPrepWarps + warp;
         if (b < a.n_bins) {
             if (a.grouped)
                 sort_and_weigh_group_bin(b, a.offsets, a.perm, a.grec, a.w, a.kappa, a.gdd, a.gxq, a.goff, a.rec,
@@ -753,11 +875,11 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
         }
         return;
     }
-    if ((int)blockIdx.x < a.n_sort_blocks + a.n_yrec_blocks) {
+    if (bid < a.n_sort_blocks + a.n_yrec_blocks) {
         // grouped gridding, per sample: entry 0 holds the offset of its first
         // y cell above its group's lowest, entries 1 .. w + 3 its y quads
         const int rqy = a.w + 4;
-        const long long e = (long long)(blockIdx.x - a.n_sort_blocks) * blockDim.x + threadIdx.x;
+        const long long e = (long long)(bid - a.n_sort_blocks) * blockDim.x + threadIdx.x;
         const long long l = e / rqy;
         if (l >= a.L) return;
         const int q = (int)(e - l * rqy);
@@ -772,7 +894,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
         }
         return;
     }
-    const int cblk = blockIdx.x - a.n_sort_blocks - a.n_yrec_blocks;
+    const int cblk = bid - a.n_sort_blocks - a.n_yrec_blocks;
     const int g = cblk / a.chunk_blocks, bx = cblk - g * a.chunk_blocks;
     const int Nk = a.Nk;
     const int warps = a.chunk_blocks * kPrepWarps;
@@ -830,10 +952,25 @@ __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(PrepTailArg
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
 }
 
-cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {
+template <int DT, bool VEC>
+__global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(const __grid_constant__ PrepTailArgs a) {
+    compensate_body<DT, VEC>(a, blockIdx.x);
+}
+
+template <int DT, bool VEC>
+__global__ void __launch_bounds__(kPrepWarps * 32)
+    compensate_multi(const __grid_constant__ BatchTable<PrepTailArgs> t) {
+    __shared__ PrepTailArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    compensate_body<DT, VEC>(sa, bid);
+}
+
+// the kernel instance: 2 x echo dtype + paired loads
+static int compensate_describe(const Plan &p, void *ws, const void *echo, const float *scale, PrepTailArgs &a,
+                               int &key) {
     char *w = reinterpret_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
-    PrepTailArgs a;
     a.n_bins = (int)p.n_bins;
     a.n_sort_blocks = (int)((p.n_bins + kPrepWarps - 1) / kPrepWarps);
     a.offsets = reinterpret_cast<const int *>(w + p.off_offsets);
@@ -866,25 +1003,53 @@ cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const f
     a.chunk_blocks = (int)cb;
     a.err = &hdr->error;
     a.shat = reinterpret_cast<float2 *>(w + p.off_shat);
-    const unsigned blocks = (unsigned)(a.n_sort_blocks + a.n_yrec_blocks + cb * ((p.n_kc + 1) / 2));
     // paired loads need an even Nk and an echo aligned to one pair
     const size_t pair_bytes = p.shape.dtype == MMSAR_ECHO_C64 ? 16 : 8;
     const bool vec = p.shape.n_k % 2 == 0 && reinterpret_cast<uintptr_t>(echo) % pair_bytes == 0;
-    switch (p.shape.dtype) {
-        case MMSAR_ECHO_C64:
-            if (vec) compensate_kernel<MMSAR_ECHO_C64, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
-            else compensate_kernel<MMSAR_ECHO_C64, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
+    key = 2 * (int)p.shape.dtype + (vec ? 1 : 0);
+    return (int)(a.n_sort_blocks + a.n_yrec_blocks + cb * ((p.n_kc + 1) / 2));
+}
+
+template <int DT, bool VEC>
+static void compensate_launch(const PrepTailArgs *a, const BatchTable<PrepTailArgs> *t, int blocks, cudaStream_t s) {
+    if (a)
+        compensate_kernel<DT, VEC><<<blocks, kPrepWarps * 32, 0, s>>>(*a);
+    else
+        compensate_multi<DT, VEC><<<blocks, kPrepWarps * 32, 0, s>>>(*t);
+}
+
+static void compensate_dispatch(int key, const PrepTailArgs *a, const BatchTable<PrepTailArgs> *t, int blocks,
+                                cudaStream_t s) {
+    switch (key) {
+        case 2 * MMSAR_ECHO_C64 + 1: compensate_launch<MMSAR_ECHO_C64, true>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_C64: compensate_launch<MMSAR_ECHO_C64, false>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_F16X2_SCALED + 1: compensate_launch<MMSAR_ECHO_F16X2_SCALED, true>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_F16X2_SCALED: compensate_launch<MMSAR_ECHO_F16X2_SCALED, false>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_BF16X2_SCALED + 1:
+            compensate_launch<MMSAR_ECHO_BF16X2_SCALED, true>(a, t, blocks, s);
             break;
-        case MMSAR_ECHO_F16X2_SCALED:
-            if (vec) compensate_kernel<MMSAR_ECHO_F16X2_SCALED, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
-            else compensate_kernel<MMSAR_ECHO_F16X2_SCALED, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
-            break;
-        default:
-            if (vec) compensate_kernel<MMSAR_ECHO_BF16X2_SCALED, true><<<blocks, kPrepWarps * 32, 0, s>>>(a);
-            else compensate_kernel<MMSAR_ECHO_BF16X2_SCALED, false><<<blocks, kPrepWarps * 32, 0, s>>>(a);
-            break;
+        default: compensate_launch<MMSAR_ECHO_BF16X2_SCALED, false>(a, t, blocks, s); break;
     }
+}
+
+cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {
+    PrepTailArgs a;
+    int key;
+    const int blocks = compensate_describe(p, ws, echo, scale, a, key);
+    compensate_dispatch(key, &a, nullptr, blocks, s);
     return cudaGetLastError();
+}
+
+cudaError_t launch_compensate_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<PrepTailArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n);
+    for (int i = 0; i < n; ++i)
+        blocks[i] = compensate_describe(r[i].plan->p, r[i].workspace, r[i].echo, r[i].echo_scale, args[i], keys[i]);
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int key, const BatchTable<PrepTailArgs> &t, int total) {
+                             compensate_dispatch(key, nullptr, &t, total, s);
+                             return cudaGetLastError();
+                         });
 }
 
 }  // namespace mmsar

@@ -60,7 +60,7 @@ constexpr int kListCap = 192;   // relevant samples listed per warp before they 
 // a 64-frequency group, lane l holding frequencies 2l and 2l + 1); WARPS: 8
 // (a 16 x 8-cell tile) or 4 (8 x 8 cells), each warp a 4 x 4-cell block.
 template <int NF, int WARPS, int NS, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) spread_kernel(SpreadArgs a) {
+__device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     constexpr int TX = 4 * (WARPS / 2);   // tile width in cells (two block rows)
     // per warp: (x-quad index, y-quad index, sample index) of each listed sample
     __shared__ int4 lists[WARPS][kListCap];
@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spread_kernel(SpreadArgs a) 
     // the frequency group varies fastest, so the groups of one tile run
     // together and share its weight records in L2
     const int n_kg = NF == 2 ? (a.n_kc + 1) / 2 : a.n_kc;
-    const int kg = blockIdx.x % n_kg;
-    const int tile = blockIdx.x / n_kg;
+    const int kg = bid % n_kg;
+    const int tile = bid / n_kg;
     // tiles outside the occupied window stay unwritten: the FFT along x'
     // reads only the window and takes the rest as zero
     if (!tile_meets((tile % tiles_x) * TX, TX, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
@@ -204,9 +204,21 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spread_kernel(SpreadArgs a) 
     }
 }
 
-cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spread_kernel(const SpreadArgs a) {
+    spread_body<NF, WARPS, NS, MINB>(a, blockIdx.x);
+}
+
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) spread_multi(const __grid_constant__ BatchTable<SpreadArgs> t) {
+    __shared__ SpreadArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    spread_body<NF, WARPS, NS, MINB>(sa, bid);
+}
+
+static int spread_describe(const Plan &p, void *ws, SpreadArgs &a) {
     char *w = reinterpret_cast<char *>(ws);
-    SpreadArgs a;
     a.shat = reinterpret_cast<const float2 *>(w + p.off_shat);
     a.dd = reinterpret_cast<const int2 *>(w + p.off_dd);
     a.wrec = reinterpret_cast<const float4 *>(w + p.off_wq);
@@ -221,20 +233,37 @@ cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     a.w = p.w;
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
+    const int nf = p.spread_nf, warps = p.spread_warps;
+    const int tiles = (p.mrx / (2 * warps)) * (p.mry / 8);
+    return tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
+}
+
+template <int NF, int WARPS, int NS, int MINB>
+static void spread_launch(const SpreadArgs *a, const BatchTable<SpreadArgs> *t, int blocks, cudaStream_t s) {
+    if (a)
+        spread_kernel<NF, WARPS, NS, MINB><<<blocks, WARPS * 32, 0, s>>>(*a);
+    else
+        spread_multi<NF, WARPS, NS, MINB><<<blocks, WARPS * 32, 0, s>>>(*t);
+}
+
+// key: 2 x frequencies per lane + (8 warps)
+static void spread_dispatch(int key, const SpreadArgs *a, const BatchTable<SpreadArgs> *t, int blocks,
+                            cudaStream_t s) {
+    switch (key) {
+        case 5: spread_launch<2, 8, 3, 2>(a, t, blocks, s); break;
+        case 4: spread_launch<2, 4, 3, 4>(a, t, blocks, s); break;
+        case 3: spread_launch<1, 8, 3, 3>(a, t, blocks, s); break;
+        default: spread_launch<1, 4, 3, 6>(a, t, blocks, s); break;
+    }
+}
+
+cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     // the launch shape is the plan's (set by mmsar_plan_set_tiles, e.g. from
     // the autotuner): NF frequencies per lane, WARPS warps per CTA; three
     // listed samples in flight
-    const int nf = p.spread_nf, warps = p.spread_warps;
-    const unsigned tiles = (unsigned)((p.mrx / (2 * warps)) * (p.mry / 8));
-    const unsigned blocks = tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
-    if (nf == 2 && warps == 8)
-        spread_kernel<2, 8, 3, 2><<<blocks, 256, 0, s>>>(a);
-    else if (nf == 2)
-        spread_kernel<2, 4, 3, 4><<<blocks, 128, 0, s>>>(a);
-    else if (warps == 8)
-        spread_kernel<1, 8, 3, 3><<<blocks, 256, 0, s>>>(a);
-    else
-        spread_kernel<1, 4, 3, 6><<<blocks, 128, 0, s>>>(a);
+    SpreadArgs a;
+    const int blocks = spread_describe(p, ws, a);
+    spread_dispatch(2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0), &a, nullptr, blocks, s);
     return cudaGetLastError();
 }
 
@@ -270,15 +299,15 @@ struct SpreadGroupArgs {
 };
 
 template <int NF, int WARPS, int NS, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) spread_groups_kernel(SpreadGroupArgs a) {
+__device__ __forceinline__ void spread_groups_body(const SpreadGroupArgs &a, int bid) {
     constexpr int TX = 4 * (WARPS / 2);
     // per warp: (x-quad index, y-quad index, sample index, last of its group)
     __shared__ int4 lists[WARPS][kListCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx / TX;
     const int n_kg = NF == 2 ? (a.n_kc + 1) / 2 : a.n_kc;
-    const int kg = blockIdx.x % n_kg;
-    const int tile = blockIdx.x / n_kg;
+    const int kg = bid % n_kg;
+    const int tile = bid / n_kg;
     if (!tile_meets((tile % tiles_x) * TX, TX, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
         !tile_meets((tile / tiles_x) * 8, 8, a.hdr->v_lo, a.hdr->v_len, a.mry))
         return;
@@ -478,9 +507,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) spread_groups_kernel(SpreadG
     }
 }
 
-cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s) {
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+    spread_groups_kernel(const __grid_constant__ SpreadGroupArgs a) {
+    spread_groups_body<NF, WARPS, NS, MINB>(a, blockIdx.x);
+}
+
+template <int NF, int WARPS, int NS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
+    spread_groups_multi(const __grid_constant__ BatchTable<SpreadGroupArgs> t) {
+    __shared__ SpreadGroupArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    spread_groups_body<NF, WARPS, NS, MINB>(sa, bid);
+}
+
+static int spread_groups_describe(const Plan &p, void *ws, SpreadGroupArgs &a) {
     char *w = reinterpret_cast<char *>(ws);
-    SpreadGroupArgs a;
     a.shat = reinterpret_cast<const float2 *>(w + p.off_shat);
     a.gdd = reinterpret_cast<const int2 *>(w + p.off_gdd);
     a.gxq = reinterpret_cast<const float4 *>(w + p.off_gxq);
@@ -501,17 +544,60 @@ cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s) {
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
     const int nf = p.spread_nf, warps = p.spread_warps;
-    const unsigned tiles = (unsigned)((p.mrx / (2 * warps)) * (p.mry / 8));
-    const unsigned blocks = tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
-    if (nf == 2 && warps == 8)
-        spread_groups_kernel<2, 8, 2, 2><<<blocks, 256, 0, s>>>(a);
-    else if (nf == 2)
-        spread_groups_kernel<2, 4, 2, 4><<<blocks, 128, 0, s>>>(a);
-    else if (warps == 8)
-        spread_groups_kernel<1, 8, 3, 2><<<blocks, 256, 0, s>>>(a);
+    const int tiles = (p.mrx / (2 * warps)) * (p.mry / 8);
+    return tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
+}
+
+template <int NF, int WARPS, int NS, int MINB>
+static void spread_groups_launch(const SpreadGroupArgs *a, const BatchTable<SpreadGroupArgs> *t, int blocks,
+                                 cudaStream_t s) {
+    if (a)
+        spread_groups_kernel<NF, WARPS, NS, MINB><<<blocks, WARPS * 32, 0, s>>>(*a);
     else
-        spread_groups_kernel<1, 4, 3, 4><<<blocks, 128, 0, s>>>(a);
+        spread_groups_multi<NF, WARPS, NS, MINB><<<blocks, WARPS * 32, 0, s>>>(*t);
+}
+
+static void spread_groups_dispatch(int key, const SpreadGroupArgs *a, const BatchTable<SpreadGroupArgs> *t,
+                                   int blocks, cudaStream_t s) {
+    switch (key) {
+        case 5: spread_groups_launch<2, 8, 2, 2>(a, t, blocks, s); break;
+        case 4: spread_groups_launch<2, 4, 2, 4>(a, t, blocks, s); break;
+        case 3: spread_groups_launch<1, 8, 3, 2>(a, t, blocks, s); break;
+        default: spread_groups_launch<1, 4, 3, 4>(a, t, blocks, s); break;
+    }
+}
+
+cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s) {
+    SpreadGroupArgs a;
+    const int blocks = spread_groups_describe(p, ws, a);
+    spread_groups_dispatch(2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0), &a, nullptr, blocks, s);
     return cudaGetLastError();
+}
+
+// Both forms: the per-sample scans grouped by launch shape, then the grouped ones.
+cudaError_t launch_spread_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<SpreadArgs> sa((size_t)n);
+    std::vector<SpreadGroupArgs> ga((size_t)n);
+    std::vector<int> sblocks((size_t)n, 0), gblocks((size_t)n, 0), keys((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const Plan &p = r[i].plan->p;
+        keys[i] = 2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0);
+        if (p.grouped)
+            gblocks[i] = spread_groups_describe(p, r[i].workspace, ga[i]);
+        else
+            sblocks[i] = spread_describe(p, r[i].workspace, sa[i]);
+    }
+    cudaError_t e = launch_groups(n, keys.data(), sa.data(), sblocks.data(),
+                                  [&](int key, const BatchTable<SpreadArgs> &t, int total) {
+                                      spread_dispatch(key, nullptr, &t, total, s);
+                                      return cudaGetLastError();
+                                  });
+    if (e != cudaSuccess) return e;
+    return launch_groups(n, keys.data(), ga.data(), gblocks.data(),
+                         [&](int key, const BatchTable<SpreadGroupArgs> &t, int total) {
+                             spread_groups_dispatch(key, nullptr, &t, total, s);
+                             return cudaGetLastError();
+                         });
 }
 
 }  // namespace mmsar

@@ -17,6 +17,7 @@
 // windows are then summed per grid point in lane order -- no atomics, a fixed
 // summation order.  The FFT then runs over the 8 columns of the CTA in shared
 // memory (fft.cuh).
+#include <algorithm>
 #include <cmath>
 
 #include "fft.cuh"
@@ -50,7 +51,7 @@ __host__ __device__ inline int stolt_warp_scratch(int nk, int WP) {
 }
 
 template <int MRZ, int WR, int GP>
-__global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
+__device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
     extern __shared__ float2 smem[];
     // GP: padded row pitch of the grid tile
     constexpr int WP = WR + 1;                            // padded pitch of a lane's window
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
     const int ncol = a.mx * a.my;
     __shared__ float turns_per_kz_s;   // (z_c - z_ref) / (2 pi): once per CTA (z_ref lives on the device)
     if (tid == 0) turns_per_kz_s = (float)((a.z_c - a.hdr->z_ref) * (0.5 / kPi));
-    const int col = blockIdx.x * kStoltCols + warp;
+    const int col = bid * kStoltCols + warp;
     for (int e = tid; e < MRZ * GP; e += 256) grid[e] = make_float2(0.f, 0.f);
     fill_twiddles<MRZ, +1>(tw, tid, 256);
     __syncthreads();
@@ -257,33 +258,82 @@ __global__ void __launch_bounds__(256) stolt_kernel(StoltArgs a) {
 }
 
 template <int MRZ, int WR, int GP>
-static cudaError_t launch_mrz_wr_gp(const StoltArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)(MRZ * GP + MRZ + kStoltCols * stolt_warp_scratch(a.nk, WR + 1)) * sizeof(float2) +
-                        (size_t)kStoltCols * 32 * sizeof(int);
-    cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR, GP>, smem);
-    if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((a.mx * a.my + kStoltCols - 1) / kStoltCols);
-    stolt_kernel<MRZ, WR, GP><<<blocks, 256, smem, s>>>(a);
+__global__ void __launch_bounds__(256) stolt_kernel(const StoltArgs a) {
+    stolt_body<MRZ, WR, GP>(a, blockIdx.x);
+}
+
+template <int MRZ, int WR, int GP>
+__global__ void __launch_bounds__(256) stolt_multi(const __grid_constant__ BatchTable<StoltArgs> t) {
+    __shared__ StoltArgs sa;
+    int bid, nb;
+    batch_args(t, batch_scan(t, bid, nb), &sa);
+    stolt_body<MRZ, WR, GP>(sa, bid);
+}
+
+static size_t stolt_smem(int MRZ, int GP, int WR, int nk) {
+    return (size_t)(MRZ * GP + MRZ + kStoltCols * stolt_warp_scratch(nk, WR + 1)) * sizeof(float2) +
+           (size_t)kStoltCols * 32 * sizeof(int);
+}
+
+static int stolt_blocks(const StoltArgs &a) { return (a.mx * a.my + kStoltCols - 1) / kStoltCols; }
+
+// one scan (a) or a fused batch (t, the largest Nk of the batch sizing the scratch)
+template <int MRZ, int WR, int GP>
+static cudaError_t launch_mrz_wr_gp(const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks, cudaStream_t s) {
+    int nk = 0;
+    if (a) {
+        nk = a->nk;
+    } else {
+        for (int i = 0; i < t->n; ++i) nk = std::max(nk, t->a[i].nk);
+    }
+    const size_t smem = stolt_smem(MRZ, GP, WR, nk);
+    if (a) {
+        cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR, GP>, smem);
+        if (e != cudaSuccess) return e;
+        stolt_kernel<MRZ, WR, GP><<<stolt_blocks(*a), 256, smem, s>>>(*a);
+    } else {
+        cudaError_t e = ensure_smem_attr((const void *)stolt_multi<MRZ, WR, GP>, smem);
+        if (e != cudaSuccess) return e;
+        stolt_multi<MRZ, WR, GP><<<blocks, 256, smem, s>>>(*t);
+    }
     return cudaGetLastError();
 }
 
 template <int MRZ, int WR>
-static cudaError_t launch_mrz_wr(const StoltArgs &a, cudaStream_t s) {
-    return launch_mrz_wr_gp<MRZ, WR, fft_pitch(kStoltCols)>(a, s);
+static cudaError_t launch_mrz_wr(const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks, cudaStream_t s) {
+    return launch_mrz_wr_gp<MRZ, WR, fft_pitch(kStoltCols)>(a, t, blocks, s);
 }
 
 // register window: w + 2 grid points rounded up to an even count
+static int stolt_wr(int w) { return w <= 6 ? 8 : (w <= 8 ? 10 : (w <= 10 ? 12 : 14)); }
+
 template <int MRZ>
-static cudaError_t launch_mrz(const StoltArgs &a, cudaStream_t s) {
-    if (a.w <= 6) return launch_mrz_wr<MRZ, 8>(a, s);
-    if (a.w <= 8) return launch_mrz_wr<MRZ, 10>(a, s);
-    if (a.w <= 10) return launch_mrz_wr<MRZ, 12>(a, s);
-    return launch_mrz_wr<MRZ, 14>(a, s);
+static cudaError_t launch_mrz(int wr, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
+                              cudaStream_t s) {
+    switch (wr) {
+        case 8: return launch_mrz_wr<MRZ, 8>(a, t, blocks, s);
+        case 10: return launch_mrz_wr<MRZ, 10>(a, t, blocks, s);
+        case 12: return launch_mrz_wr<MRZ, 12>(a, t, blocks, s);
+        default: return launch_mrz_wr<MRZ, 14>(a, t, blocks, s);
+    }
 }
 
-cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
+// key: MRZ x 16 + register window
+static cudaError_t stolt_dispatch(int key, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
+                                  cudaStream_t s) {
+    const int wr = key & 15;
+    switch (key >> 4) {
+        case 32: return launch_mrz<32>(wr, a, t, blocks, s);
+        case 64: return launch_mrz<64>(wr, a, t, blocks, s);
+        case 128: return launch_mrz<128>(wr, a, t, blocks, s);
+        case 256: return launch_mrz<256>(wr, a, t, blocks, s);
+        case 512: return launch_mrz<512>(wr, a, t, blocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static int stolt_describe(const Plan &p, void *ws, StoltArgs &a) {
     char *w = reinterpret_cast<char *>(ws);
-    StoltArgs a;
     a.S = reinterpret_cast<const float2 *>(w + p.off_S);
     a.Z = reinterpret_cast<float2 *>(w + p.off_Z);
     a.hdr = reinterpret_cast<const WsHeader *>(w);
@@ -304,14 +354,26 @@ cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
     a.kappa = (float)(1.5 * kPi / p.w);
     a.deapod_scale = (float)(std::sqrt(kPi / p.tau_z) / p.mrz);
     a.tau_z = (float)p.tau_z;
-    switch (p.mrz) {
-        case 32: return launch_mrz<32>(a, s);
-        case 64: return launch_mrz<64>(a, s);
-        case 128: return launch_mrz<128>(a, s);
-        case 256: return launch_mrz<256>(a, s);
-        case 512: return launch_mrz<512>(a, s);
-        default: return cudaErrorInvalidValue;
+    return p.mrz * 16 + stolt_wr(p.w);
+}
+
+cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
+    StoltArgs a;
+    const int key = stolt_describe(p, ws, a);
+    return stolt_dispatch(key, &a, nullptr, 0, s);
+}
+
+cudaError_t launch_stolt_multi(const mmsar_request *r, int n, cudaStream_t s) {
+    std::vector<StoltArgs> args((size_t)n);
+    std::vector<int> blocks((size_t)n), keys((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        keys[i] = stolt_describe(r[i].plan->p, r[i].workspace, args[i]);
+        blocks[i] = stolt_blocks(args[i]);
     }
+    return launch_groups(n, keys.data(), args.data(), blocks.data(),
+                         [&](int key, const BatchTable<StoltArgs> &t, int total) {
+                             return stolt_dispatch(key, nullptr, &t, total, s);
+                         });
 }
 
 }  // namespace mmsar

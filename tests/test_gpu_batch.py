@@ -50,6 +50,61 @@ def test_batch_equals_single(dev):
         assert rma.nmse(got, rma.rma_exact(rma.setup_from(s))) <= 2e-5
 
 
+def test_fused_batch_equals_single(dev):
+    """One fused launch per stage and kernel shape reproduces every scan's
+    own image bit for bit: uneven shapes, FP32 and FP16 echoes, different
+    gridding launch shapes and the grouped form in one batch."""
+    from paper_2305_02064_gb300.batch import ScanJob, image_batch_fused
+    scans = small_mix(8)
+    jobs = [ScanJob(s, dev, dtype="f16" if i % 3 == 2 else "c64") for i, s in enumerate(scans)]
+    shapes = [(2, 4, 0), (1, 8, 0), (2, 8, 1), (1, 4, 0)]
+    for i, j in enumerate(jobs):
+        j.plan.set_tiles(*shapes[i % len(shapes)])
+    single = []
+    for j in jobs:
+        j.image()
+        single.append(j.vol.cpu().numpy())
+        j.vol.fill_(0)
+    n = image_batch_fused(jobs)
+    torch.cuda.synchronize()
+    assert 0 < n < 10 * len(jobs)
+    for j, ref in zip(jobs, single):
+        assert np.array_equal(j.vol.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+        j.plan.poll_error(j.ws)
+
+
+def test_fused_batch_beyond_one_table(dev):
+    """More scans than one fused launch takes (32): the groups split into
+    several launches, the images stay bit-identical."""
+    from paper_2305_02064_gb300.batch import ScanJob, image_batch_fused
+    scans = [small_mix(1)[0]] * 20 + small_mix(20)
+    jobs = [ScanJob(s, dev) for s in scans]
+    single = []
+    for j in jobs:
+        j.image()
+        single.append(j.vol.cpu().numpy())
+        j.vol.fill_(0)
+    image_batch_fused(jobs)
+    torch.cuda.synchronize()
+    for j, ref in zip(jobs, single):
+        assert np.array_equal(j.vol.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
+def test_fused_graph_replay_equals_eager(dev):
+    from paper_2305_02064_gb300.batch import BatchGraph, ScanJob
+    scans = small_mix(5)
+    jobs = [ScanJob(s, dev) for s in scans]
+    g = BatchGraph(jobs, fused=True)
+    eager = [j.vol.clone() for j in jobs]
+    for j in jobs:
+        j.vol.fill_(0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert 0 < g.launches < 10 * len(jobs)
+    for j, e in zip(jobs, eager):
+        assert torch.equal(j.vol.view(torch.float32), e.view(torch.float32))
+
+
 def test_graph_replay_equals_eager(dev):
     from paper_2305_02064_gb300.batch import BatchGraph, ScanJob
     scans = small_mix(4)
