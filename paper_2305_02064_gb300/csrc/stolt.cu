@@ -11,12 +11,13 @@
 // spread onto an oversampled periodic grid of MRZ points, the grid is
 // transformed by an inverse FFT and the Gaussian is deconvolved.
 //
-// One warp per column.  Because k_z grows with k, the samples of a column
-// are already sorted along the gridding axis: each lane spreads a contiguous
-// run of them into a small window of grid points kept in registers, and the
-// windows are then summed per grid point in lane order -- no atomics, a fixed
-// summation order.  The FFT then runs over the 8 columns of the CTA in shared
-// memory (fft.cuh).
+// One warp per column, or per pair of mirror columns (+-k_x, k_y), which
+// share every k_z sample position, phase factor and weight.  Because k_z grows with k, the samples of a column are already
+// sorted along the gridding axis: each lane spreads a contiguous run of them
+// into a small window of grid points kept in registers (one window per column
+// of the pair), and the windows are then summed per grid point in lane order
+// -- no atomics, a fixed summation order.  The FFT then runs over the columns
+// of the CTA in shared memory (fft.cuh).
 #include <algorithm>
 #include <cmath>
 
@@ -42,42 +43,68 @@ struct StoltArgs {
 constexpr int kStoltCols = 8;
 
 // complex elements of a warp's scratch region (even, so every region starts
-// on 16 bytes): the larger of 32 lane windows of WP points and the fallback's
-// staged samples (nk values + nk floats)
-__host__ __device__ inline int stolt_warp_scratch(int nk, int WP) {
-    const int a = 32 * WP, b = nk + (nk + 1) / 2;
+// on 16 bytes): the larger of the lanes' windows of WP points for NC
+// columns and the fallback's staged samples of one column (nk values + nk
+// floats)
+__host__ __device__ inline int stolt_warp_scratch(int nk, int WP, int NC) {
+    const int a = NC * 32 * WP, b = nk + (nk + 1) / 2;
     const int m = a > b ? a : b;
     return (m + 1) & ~1;
 }
 
-template <int MRZ, int WR, int GP>
+// NC = 1: warp w of block b takes spectral column 8 b + w.  NC = 2: it takes
+// the mirror pair (k_x, k_y), (-k_x, k_y) -- pair (cx, n), cx <= Mx/2, one or
+// two columns (index 0 and Mx/2 have no mirror on the grid).  The columns of
+// a pair share k_x^2 + k_y^2 and hence every k_z sample position, phase
+// factor and Gaussian weight (computed once, bit for bit as for a single
+// column); only the spectrum values differ.  GP: row pitch of the grid tile
+// of 8 NC columns.
+template <int MRZ, int WR, int GP, int NC>
 __device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
     extern __shared__ float2 smem[];
-    // GP: padded row pitch of the grid tile
     constexpr int WP = WR + 1;                            // padded pitch of a lane's window
-    float2 *grid = smem;                                  // [MRZ][GP]
+    float2 *grid = smem;                                  // [MRZ][GP], column warp * NC + ci
     float2 *tw = grid + MRZ * GP;                         // [MRZ]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // per-warp scratch: either the lanes' register windows [32][WP] or, on the
-    // fallback path, the staged samples (values [nk], grid positions [nk])
-    const int wscr = stolt_warp_scratch(a.nk, WP);
+    // per-warp scratch: either the lanes' register windows [NC][32][WP] or, on
+    // the fallback path, one column's staged samples (values [nk], grid positions [nk])
+    const int wscr = stolt_warp_scratch(a.nk, WP, NC);
     float2 *scratch = tw + MRZ + warp * wscr;
     int *jlo_s = reinterpret_cast<int *>(tw + MRZ + kStoltCols * wscr);   // [8 * 32]
-    const int ncol = a.mx * a.my;
     __shared__ float turns_per_kz_s;   // (z_c - z_ref) / (2 pi): once per CTA (z_ref lives on the device)
     if (tid == 0) turns_per_kz_s = (float)((a.z_c - a.hdr->z_ref) * (0.5 / kPi));
-    const int col = bid * kStoltCols + warp;
+    // the warp's columns (-1: none) and their shared (k_x, k_y) magnitudes
+    int cols[NC];
+    int om, on;
+    bool live;
+    if constexpr (NC == 1) {
+        const int col = bid * kStoltCols + warp;
+        live = col < a.mx * a.my;
+        om = col / a.my;
+        on = col - om * a.my;
+        cols[0] = live ? col : -1;
+    } else {
+        static_assert(NC == 2, "one column or a mirror pair per warp");
+        const int cls = bid * kStoltCols + warp;
+        live = cls < (a.mx / 2 + 1) * a.my;
+        om = cls / a.my;
+        on = cls - om * a.my;
+        const bool px = om > 0 && om < a.mx / 2;
+        cols[0] = live ? om * a.my + on : -1;
+        cols[1] = live && px ? (a.mx - om) * a.my + on : -1;
+    }
     for (int e = tid; e < MRZ * GP; e += 256) grid[e] = make_float2(0.f, 0.f);
     fill_twiddles<MRZ, +1>(tw, tid, 256);
     __syncthreads();
-    if (col < ncol) {
-        const int om = col / a.my, on = col - (col / a.my) * a.my;
+    if (live) {
         const float kx = (float)(om - a.mx / 2) * a.kx_step;
         const float ky = (float)(on - a.my / 2) * a.ky_step;
         const float kr2 = kx * kx + ky * ky;
         const float turns_per_kz = turns_per_kz_s;
         const float cells_per_kz = a.cells_per_kz;
-        const float2 *Sc = a.S + (long long)col * a.nkp;
+        const float2 *Sc[NC];
+#pragma unroll
+        for (int ci = 0; ci < NC; ++ci) Sc[ci] = a.S + (long long)(cols[ci] < 0 ? 0 : cols[ci]) * a.nkp;
         const float hw = 0.5f * a.w;
         // k = 2 pi f / c on the uniform grid, formed as k0_hi + (k0_lo + k dk)
         // (k0 split into two floats): within half an ulp of the FP64 value
@@ -92,17 +119,20 @@ __device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
             const bool evan = k < a.nk && 4.f * kv * kv - kr2 <= 0.f;
             kf += __popc(__ballot_sync(0xffffffffu, evan));
         }
-        // Eq. 14-15 for one sample: grid position t (cells) and weighted value c
-        auto sample = [&](int k, float &t, float2 &c) {
+        // Eq. 14-15 for one sample: grid position t (cells), k_z and the phase
+        // factor exp(+j k_z (z_c - z_ref)); the weighted value of column ci is
+        // then c = S(k) k_z (cs, sn)
+        auto geometry = [&](int k, float &t, float &kz, float &cs, float &sn) {
             const float kv = wavenumber(k);
-            const float kz = sqrtf(4.f * kv * kv - kr2);
+            kz = sqrtf(4.f * kv * kv - kr2);
             t = kz * cells_per_kz;
             float ph = kz * turns_per_kz;
             ph -= rintf(ph);                        // [-1/2, 1/2] turn
-            float sn, cs;
             __sincosf(6.283185307179586f * ph, &sn, &cs);
-            const float2 sv = __ldg(Sc + k);
-            c = cmul(make_float2(sv.x * kz, sv.y * kz), make_float2(cs, sn));
+        };
+        auto value = [&](int ci, int k, float kz, float cs, float sn) {
+            const float2 sv = __ldg(Sc[ci] + k);
+            return cmul(make_float2(sv.x * kz, sv.y * kz), make_float2(cs, sn));
         };
         if (kf < a.nk) {
             // Each lane spreads a contiguous run of samples (sorted along the
@@ -110,7 +140,7 @@ __device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
             // the Gaussian weights of consecutive points follow the recurrence
             // w_{i+1} = w_i r_i, r_{i+1} = r_i exp(-2 kappa).
             const int nv = a.nk - kf;
-            // grid position of sample k (as sample() computes it)
+            // grid position of sample k (as geometry() computes it)
             auto grid_pos = [&](int k) {
                 const float kv = wavenumber(k);
                 return sqrtf(4.f * kv * kv - kr2) * cells_per_kz;
@@ -154,33 +184,44 @@ __device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
                 fits = k_beg >= k_end || (int)ceilf(grid_pos(k_end - 1) - hw) + a.w - 1 - jl + 1 <= WR;
             }
             if (__all_sync(0xffffffffu, fits)) {
-                float2 acc[WR];
+                float2 acc[NC][WR];
 #pragma unroll
-                for (int i = 0; i < WR; ++i) acc[i] = make_float2(0.f, 0.f);
+                for (int ci = 0; ci < NC; ++ci)
+#pragma unroll
+                    for (int i = 0; i < WR; ++i) acc[ci][i] = make_float2(0.f, 0.f);
                 const float qk = __expf(-2.f * a.kappa);
                 for (int k = k_beg; k < k_end; ++k) {
-                    float t;
-                    float2 c;
-                    sample(k, t, c);
+                    float t, kz, cs, sn;
+                    geometry(k, t, kz, cs, sn);
                     const float d0 = t - (float)jl;
                     float wgt = __expf(-a.kappa * d0 * d0);
                     float rho = __expf(a.kappa * (2.f * d0 - 1.f));
                     // weights and ratios advance together: (w, r) *= (r, q)
+                    float wv[WR];
                     float2 wr = make_float2(wgt, rho);
 #pragma unroll
                     for (int i = 0; i < WR; ++i) {
-                        acc[i] = ffma2(make_float2(wr.x, wr.x), c, acc[i]);
+                        wv[i] = wr.x;
                         wr = fmul2(wr, make_float2(wr.y, qk));
                     }
-                }
-                float2 *mine = scratch + lane * WP;
 #pragma unroll
-                for (int i = 0; i < WR; ++i) mine[i] = acc[i];
+                    for (int ci = 0; ci < NC; ++ci) {
+                        if (cols[ci] < 0) continue;
+                        const float2 c = value(ci, k, kz, cs, sn);
+#pragma unroll
+                        for (int i = 0; i < WR; ++i) acc[ci][i] = ffma2(make_float2(wv[i], wv[i]), c, acc[ci][i]);
+                    }
+                }
+#pragma unroll
+                for (int ci = 0; ci < NC; ++ci) {
+                    float2 *mine = scratch + (ci * 32 + lane) * WP;
+#pragma unroll
+                    for (int i = 0; i < WR; ++i) mine[i] = acc[ci][i];
+                }
                 jlo_s[warp * 32 + lane] = jl;
                 __syncwarp();
                 // sum the windows per grid point, lanes in a fixed order
                 const int *jw = jlo_s + warp * 32;
-                const float2 *wb = scratch;
                 const int J_lo = jw[0], J_hi = jw[nact - 1] + WR - 1;
                 for (int jb = J_lo; jb <= J_hi; jb += 32) {
                     const int j = jb + lane;
@@ -193,141 +234,178 @@ __device__ __forceinline__ void stolt_body(const StoltArgs &a, int bid) {
                             const int mid = (lo + hi) >> 1;
                             if (jw[mid] < j - WR + 1) lo = mid + 1; else hi = mid;
                         }
-                        float2 sum = make_float2(0.f, 0.f);
-                        for (int l2 = lo; l2 < nact; ++l2) {
-                            const int o = j - jw[l2];
-                            if (o < 0) break;
-                            sum = cadd(sum, wb[l2 * WP + o]);
+#pragma unroll
+                        for (int ci = 0; ci < NC; ++ci) {
+                            if (cols[ci] < 0) continue;
+                            const float2 *wb = scratch + ci * 32 * WP;
+                            float2 sum = make_float2(0.f, 0.f);
+                            for (int l2 = lo; l2 < nact; ++l2) {
+                                const int o = j - jw[l2];
+                                if (o < 0) break;
+                                sum = cadd(sum, wb[l2 * WP + o]);
+                            }
+                            float2 &gref = grid[(j & (MRZ - 1)) * GP + warp * NC + ci];
+                            gref = cadd(gref, sum);
                         }
-                        float2 &gref = grid[(j & (MRZ - 1)) * GP + warp];
-                        gref = cadd(gref, sum);
                     }
                     __syncwarp();
                 }
             } else {
                 // a run that spans more than the register window (very coarse
-                // depth sampling): stage the samples and gather each grid
-                // point from the samples in reach, found by binary search
+                // depth sampling): stage one column's samples at a time and
+                // gather each grid point from the samples in reach, found by
+                // binary search
                 float2 *cw = scratch;
                 float *tw_ = reinterpret_cast<float *>(scratch + a.nk);
                 for (int k = kf + lane; k < a.nk; k += 32) {
-                    float t;
-                    float2 c;
-                    sample(k, t, c);
-                    cw[k] = c;
+                    float t, kz, cs, sn;
+                    geometry(k, t, kz, cs, sn);
                     tw_[k] = t;
                 }
                 __syncwarp();
                 const int jlo = (int)ceilf(tw_[kf] - hw);
                 const int jhi = (int)ceilf(tw_[a.nk - 1] - hw) + a.w - 1;
-                for (int jb = jlo; jb <= jhi; jb += 32) {
-                    const int j = jb + lane;
-                    if (j <= jhi) {
-                        const float lo_t = (float)j - hw, hi_t = (float)j + hw;
-                        int lo = kf, hi = a.nk;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (tw_[mid] > lo_t) hi = mid; else lo = mid + 1;
-                        }
-                        float2 acc = make_float2(0.f, 0.f);
-                        for (int k = lo; k < a.nk && tw_[k] <= hi_t; ++k) {
-                            const float d = tw_[k] - (float)j;
-                            const float wgt = __expf(-a.kappa * d * d);
-                            acc.x = fmaf(wgt, cw[k].x, acc.x);
-                            acc.y = fmaf(wgt, cw[k].y, acc.y);
-                        }
-                        float2 &gref = grid[(j & (MRZ - 1)) * GP + warp];
-                        gref = cadd(gref, acc);
+#pragma unroll
+                for (int ci = 0; ci < NC; ++ci) {
+                    if (cols[ci] < 0) continue;
+                    for (int k = kf + lane; k < a.nk; k += 32) {
+                        float t, kz, cs, sn;
+                        geometry(k, t, kz, cs, sn);
+                        cw[k] = value(ci, k, kz, cs, sn);
                     }
                     __syncwarp();
+                    for (int jb = jlo; jb <= jhi; jb += 32) {
+                        const int j = jb + lane;
+                        if (j <= jhi) {
+                            const float lo_t = (float)j - hw, hi_t = (float)j + hw;
+                            int lo = kf, hi = a.nk;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (tw_[mid] > lo_t) hi = mid; else lo = mid + 1;
+                            }
+                            float2 acc = make_float2(0.f, 0.f);
+                            for (int k = lo; k < a.nk && tw_[k] <= hi_t; ++k) {
+                                const float d = tw_[k] - (float)j;
+                                const float wgt = __expf(-a.kappa * d * d);
+                                acc.x = fmaf(wgt, cw[k].x, acc.x);
+                                acc.y = fmaf(wgt, cw[k].y, acc.y);
+                            }
+                            float2 &gref = grid[(j & (MRZ - 1)) * GP + warp * NC + ci];
+                            gref = cadd(gref, acc);
+                        }
+                        __syncwarp();
+                    }
                 }
             }
         }
     }
     __syncthreads();
-    smem_fft<MRZ, kStoltCols, 256, +1, GP>(grid, tw);
-    if (col < ncol) {
-        float2 *Zc = a.Z + (long long)col * a.nz;
+    smem_fft<MRZ, kStoltCols * NC, 256, +1, GP>(grid, tw);
+#pragma unroll
+    for (int ci = 0; ci < NC; ++ci) {
+        if (cols[ci] < 0) continue;
+        float2 *Zc = a.Z + (long long)cols[ci] * a.nz;
         for (int q = lane; q < a.nz; q += 32) {
             const int qp = q - a.nz / 2;
             const float sc = a.deapod_scale * __expf((float)(qp * qp) * a.tau_z);
-            const float2 v = grid[(qp & (MRZ - 1)) * GP + warp];
+            const float2 v = grid[(qp & (MRZ - 1)) * GP + warp * NC + ci];
             Zc[q] = make_float2(v.x * sc, v.y * sc);
         }
     }
 }
 
-template <int MRZ, int WR, int GP>
-__global__ void __launch_bounds__(256) stolt_kernel(const StoltArgs a) {
-    stolt_body<MRZ, WR, GP>(a, blockIdx.x);
+// NC = 2 takes three CTAs per SM (the register bound); NC = 1 as many as fit
+template <int MRZ, int WR, int GP, int NC>
+__global__ void __launch_bounds__(256, NC == 2 ? 3 : 1) stolt_kernel(const StoltArgs a) {
+    stolt_body<MRZ, WR, GP, NC>(a, blockIdx.x);
 }
 
-template <int MRZ, int WR, int GP>
-__global__ void __launch_bounds__(256) stolt_multi(const __grid_constant__ BatchTable<StoltArgs> t) {
+template <int MRZ, int WR, int GP, int NC>
+__global__ void __launch_bounds__(256, NC == 2 ? 3 : 1)
+    stolt_multi(const __grid_constant__ BatchTable<StoltArgs> t) {
     __shared__ StoltArgs sa;
     int bid, nb;
     batch_args(t, batch_scan(t, bid, nb), &sa);
-    stolt_body<MRZ, WR, GP>(sa, bid);
+    stolt_body<MRZ, WR, GP, NC>(sa, bid);
 }
 
-static size_t stolt_smem(int MRZ, int GP, int WR, int nk) {
-    return (size_t)(MRZ * GP + MRZ + kStoltCols * stolt_warp_scratch(nk, WR + 1)) * sizeof(float2) +
+// grid tile pitch: 8 NC columns plus one (consecutive grid points of one
+// column then fall on different banks)
+__host__ __device__ constexpr int stolt_pitch(int NC) { return kStoltCols * NC + 1; }
+
+static size_t stolt_smem(int MRZ, int WR, int NC, int nk) {
+    return (size_t)(MRZ * stolt_pitch(NC) + MRZ + kStoltCols * stolt_warp_scratch(nk, WR + 1, NC)) * sizeof(float2) +
            (size_t)kStoltCols * 32 * sizeof(int);
 }
 
-static int stolt_blocks(const StoltArgs &a) { return (a.mx * a.my + kStoltCols - 1) / kStoltCols; }
+// mirror pairs for the 8-point window (w <= 6; two windows of more points
+// no longer fit the registers) when three CTAs also fit in shared memory
+static int stolt_nc(int MRZ, int WR, int nk) {
+    return WR == 8 && MRZ <= 256 && stolt_smem(MRZ, WR, 2, nk) <= 75 * 1024 ? 2 : 1;
+}
+
+static int stolt_blocks(const StoltArgs &a, int nc) {
+    const int units = nc == 2 ? (a.mx / 2 + 1) * a.my : a.mx * a.my;
+    return (units + kStoltCols - 1) / kStoltCols;
+}
 
 // one scan (a) or a fused batch (t, the largest Nk of the batch sizing the scratch)
-template <int MRZ, int WR, int GP>
-static cudaError_t launch_mrz_wr_gp(const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks, cudaStream_t s) {
+template <int MRZ, int WR, int NC>
+static cudaError_t launch_mrz_wr_nc(const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks, cudaStream_t s) {
+    constexpr int GP = stolt_pitch(NC);
     int nk = 0;
     if (a) {
         nk = a->nk;
     } else {
         for (int i = 0; i < t->n; ++i) nk = std::max(nk, t->a[i].nk);
     }
-    const size_t smem = stolt_smem(MRZ, GP, WR, nk);
+    const size_t smem = stolt_smem(MRZ, WR, NC, nk);
     if (a) {
-        cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR, GP>, smem);
+        cudaError_t e = ensure_smem_attr((const void *)stolt_kernel<MRZ, WR, GP, NC>, smem);
         if (e != cudaSuccess) return e;
-        stolt_kernel<MRZ, WR, GP><<<stolt_blocks(*a), 256, smem, s>>>(*a);
+        stolt_kernel<MRZ, WR, GP, NC><<<stolt_blocks(*a, NC), 256, smem, s>>>(*a);
     } else {
-        cudaError_t e = ensure_smem_attr((const void *)stolt_multi<MRZ, WR, GP>, smem);
+        cudaError_t e = ensure_smem_attr((const void *)stolt_multi<MRZ, WR, GP, NC>, smem);
         if (e != cudaSuccess) return e;
-        stolt_multi<MRZ, WR, GP><<<blocks, 256, smem, s>>>(*t);
+        stolt_multi<MRZ, WR, GP, NC><<<blocks, 256, smem, s>>>(*t);
     }
     return cudaGetLastError();
 }
 
 template <int MRZ, int WR>
-static cudaError_t launch_mrz_wr(const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks, cudaStream_t s) {
-    return launch_mrz_wr_gp<MRZ, WR, fft_pitch(kStoltCols)>(a, t, blocks, s);
+static cudaError_t launch_mrz_wr(int nc, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
+                                 cudaStream_t s) {
+    if constexpr (WR == 8 && MRZ <= 256)   // (a 512-point tile of mirror pairs exceeds the budget)
+        if (nc == 2) return launch_mrz_wr_nc<MRZ, WR, 2>(a, t, blocks, s);
+    return launch_mrz_wr_nc<MRZ, WR, 1>(a, t, blocks, s);
 }
 
 // register window: w + 2 grid points rounded up to an even count
 static int stolt_wr(int w) { return w <= 6 ? 8 : (w <= 8 ? 10 : (w <= 10 ? 12 : 14)); }
 
 template <int MRZ>
-static cudaError_t launch_mrz(int wr, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
+static cudaError_t launch_mrz(int wr, int nc, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
                               cudaStream_t s) {
     switch (wr) {
-        case 8: return launch_mrz_wr<MRZ, 8>(a, t, blocks, s);
-        case 10: return launch_mrz_wr<MRZ, 10>(a, t, blocks, s);
-        case 12: return launch_mrz_wr<MRZ, 12>(a, t, blocks, s);
-        default: return launch_mrz_wr<MRZ, 14>(a, t, blocks, s);
+        case 8: return launch_mrz_wr<MRZ, 8>(nc, a, t, blocks, s);
+        case 10: return launch_mrz_wr<MRZ, 10>(nc, a, t, blocks, s);
+        case 12: return launch_mrz_wr<MRZ, 12>(nc, a, t, blocks, s);
+        default: return launch_mrz_wr<MRZ, 14>(nc, a, t, blocks, s);
     }
 }
 
-// key: MRZ x 16 + register window
+// key: MRZ << 8 | register window << 2 | mirror pairs
+static int stolt_key_nc(int key) { return (key & 1) ? 2 : 1; }
+
 static cudaError_t stolt_dispatch(int key, const StoltArgs *a, const BatchTable<StoltArgs> *t, int blocks,
                                   cudaStream_t s) {
-    const int wr = key & 15;
-    switch (key >> 4) {
-        case 32: return launch_mrz<32>(wr, a, t, blocks, s);
-        case 64: return launch_mrz<64>(wr, a, t, blocks, s);
-        case 128: return launch_mrz<128>(wr, a, t, blocks, s);
-        case 256: return launch_mrz<256>(wr, a, t, blocks, s);
-        case 512: return launch_mrz<512>(wr, a, t, blocks, s);
+    const int wr = (key >> 2) & 63, nc = stolt_key_nc(key);
+    switch (key >> 8) {
+        case 32: return launch_mrz<32>(wr, nc, a, t, blocks, s);
+        case 64: return launch_mrz<64>(wr, nc, a, t, blocks, s);
+        case 128: return launch_mrz<128>(wr, nc, a, t, blocks, s);
+        case 256: return launch_mrz<256>(wr, nc, a, t, blocks, s);
+        case 512: return launch_mrz<512>(wr, nc, a, t, blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -354,7 +432,8 @@ static int stolt_describe(const Plan &p, void *ws, StoltArgs &a) {
     a.kappa = (float)(1.5 * kPi / p.w);
     a.deapod_scale = (float)(std::sqrt(kPi / p.tau_z) / p.mrz);
     a.tau_z = (float)p.tau_z;
-    return p.mrz * 16 + stolt_wr(p.w);
+    const int wr = stolt_wr(p.w);
+    return (p.mrz << 8) | (wr << 2) | (stolt_nc(p.mrz, wr, a.nk) / 2);
 }
 
 cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s) {
@@ -368,7 +447,7 @@ cudaError_t launch_stolt_multi(const mmsar_request *r, int n, cudaStream_t s) {
     std::vector<int> blocks((size_t)n), keys((size_t)n);
     for (int i = 0; i < n; ++i) {
         keys[i] = stolt_describe(r[i].plan->p, r[i].workspace, args[i]);
-        blocks[i] = stolt_blocks(args[i]);
+        blocks[i] = stolt_blocks(args[i], stolt_key_nc(keys[i]));
     }
     return launch_groups(n, keys.data(), args.data(), blocks.data(),
                          [&](int key, const BatchTable<StoltArgs> &t, int total) {
