@@ -295,4 +295,127 @@ __device__ __forceinline__ void reg_dft(float2 *v) {
     }
 }
 
+// ---------------------------------------------------------------- column pairs
+// Two columns' complex values in split form: re = (re_a, re_b), im =
+// (im_a, im_b).  Every packed two-lane instruction then serves both columns,
+// and a multiplication by +-i is a swap of the halves folded into the next
+// addition.  The DFTs below are those of reg_dft, column by column.
+struct cpair {
+    float2 re, im;
+};
+__device__ __forceinline__ cpair padd(cpair a, cpair b) { return {fadd2(a.re, b.re), fadd2(a.im, b.im)}; }
+__device__ __forceinline__ cpair psub(cpair a, cpair b) { return {fsub2(a.re, b.re), fsub2(a.im, b.im)}; }
+// a + SIGN i b and a - SIGN i b
+template <int SIGN>
+__device__ __forceinline__ cpair padd_si(cpair a, cpair b) {
+    return SIGN > 0 ? cpair{fsub2(a.re, b.im), fadd2(a.im, b.re)} : cpair{fadd2(a.re, b.im), fsub2(a.im, b.re)};
+}
+template <int SIGN>
+__device__ __forceinline__ cpair psub_si(cpair a, cpair b) {
+    return SIGN > 0 ? cpair{fadd2(a.re, b.im), fsub2(a.im, b.re)} : cpair{fsub2(a.re, b.im), fadd2(a.im, b.re)};
+}
+// a (c + i s) with (c, s) broadcast to both columns
+__device__ __forceinline__ cpair pmul_cs(cpair a, float c, float s) {
+    const float2 cc = make_float2(c, c), ss = make_float2(s, s);
+    return {fsub2(fmul2(a.re, cc), fmul2(a.im, ss)), ffma2(a.re, ss, fmul2(a.im, cc))};
+}
+
+template <int SIGN>
+__device__ __forceinline__ void pdft4(cpair &a0, cpair &a1, cpair &a2, cpair &a3) {
+    const cpair t0 = padd(a0, a2), t1 = psub(a0, a2);
+    const cpair t2 = padd(a1, a3), d = psub(a1, a3);
+    a0 = padd(t0, t2);
+    a2 = psub(t0, t2);
+    a1 = padd_si<SIGN>(t1, d);   // t1 + SIGN i d
+    a3 = psub_si<SIGN>(t1, d);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void pdft8(cpair *v) {
+    cpair e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    cpair o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    pdft4<SIGN>(e0, e1, e2, e3);
+    pdft4<SIGN>(o0, o1, o2, o3);
+    const float2 r = make_float2(0.70710678118654752440f, 0.70710678118654752440f);
+    // o1 *= r (1 + SIGN i), o3 *= r (-1 + SIGN i); o2 *= SIGN i folds into the additions
+    if (SIGN > 0) {
+        o1 = {fmul2(fsub2(o1.re, o1.im), r), fmul2(fadd2(o1.im, o1.re), r)};
+        o3 = {fmul2(fadd2(o3.re, o3.im), make_float2(-r.x, -r.y)), fmul2(fsub2(o3.re, o3.im), r)};
+    } else {
+        o1 = {fmul2(fadd2(o1.re, o1.im), r), fmul2(fsub2(o1.im, o1.re), r)};
+        o3 = {fmul2(fsub2(o3.im, o3.re), r), fmul2(fadd2(o3.re, o3.im), make_float2(-r.x, -r.y))};
+    }
+    v[0] = padd(e0, o0); v[4] = psub(e0, o0);
+    v[1] = padd(e1, o1); v[5] = psub(e1, o1);
+    v[2] = padd_si<SIGN>(e2, o2); v[6] = psub_si<SIGN>(e2, o2);
+    v[3] = padd(e3, o3); v[7] = psub(e3, o3);
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void pdft_r(cpair *v) {
+    if constexpr (R == 8) {
+        pdft8<SIGN>(v);
+    } else if constexpr (R == 4) {
+        pdft4<SIGN>(v[0], v[1], v[2], v[3]);
+    } else {
+        const cpair a = v[0], b = v[1];
+        v[0] = padd(a, b);
+        v[1] = psub(a, b);
+    }
+}
+
+// a * exp(SIGN 2 pi i M / N) on a column pair, M and N compile-time
+template <int N, int M, int SIGN>
+__device__ __forceinline__ cpair ptwiddle_ct(cpair a) {
+    constexpr int m = ((M % N) + N) % N;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (2 * m == N) {
+        const float2 neg = make_float2(-1.f, -1.f);
+        return {fmul2(a.re, neg), fmul2(a.im, neg)};
+    } else if constexpr (4 * m == N || 4 * m == 3 * N) {
+        // times +-i: (re, im) -> (-+im, +-re)
+        constexpr int S = (4 * m == N) ? SIGN : -SIGN;
+        const float2 neg = make_float2(-1.f, -1.f);
+        return S > 0 ? cpair{fmul2(a.im, neg), a.re} : cpair{a.im, fmul2(a.re, neg)};
+    } else {
+        constexpr float c = (float)ct_cos_turn(m, N);
+        constexpr float s = (float)(SIGN * ct_sin_turn(m, N));
+        return pmul_cs(a, c, s);
+    }
+}
+
+// In-place DFT of v[0..N-1] for both columns of the pairs (natural order in
+// and out), the same decomposition as reg_dft.
+template <int N, int SIGN>
+__device__ __forceinline__ void preg_dft(cpair *v) {
+    if constexpr (N <= 8) {
+        pdft_r<N, SIGN>(v);
+    } else {
+        constexpr int R1 = N == 16 ? 4 : 8;
+        constexpr int N2 = N / R1;
+        cpair t[N];
+        static_for<N2>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            cpair a[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[n2 + N2 * n1];
+            pdft_r<R1, SIGN>(a);
+            static_for<R1>([&](auto k1c) {
+                constexpr int k1 = decltype(k1c)::value;
+                t[n2 * R1 + k1] = ptwiddle_ct<N, n2 * k1, SIGN>(a[k1]);
+            });
+        });
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            cpair b[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) b[n2] = t[n2 * R1 + k1];
+            preg_dft<N2, SIGN>(b);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) v[k1 + R1 * k2] = b[k2];
+        }
+    }
+}
+
 }  // namespace mmsar

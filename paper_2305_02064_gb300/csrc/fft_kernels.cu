@@ -107,7 +107,11 @@ __host__ __device__ constexpr int reg_fft_pitch(int L) {
     return reg_fft_n1(L) * fft_cols(L) + (fft_cols(L) < 32 ? 8 : 0);
 }
 
-template <int L, int SIGN>
+// PAIR: step 1 on pairs of adjacent columns (16-byte loads, the window test
+// and the inter-step twiddle shared by the two, the DFT in split form:
+// cpair in fft.cuh); needs 16-byte aligned rows and two step-1 columns per
+// thread.
+template <int L, int SIGN, bool PAIR>
 __device__ __forceinline__ void column_fft_reg_body(const ColumnFFT &a, int bx, int by) {
     constexpr int N1 = reg_fft_n1(L), N2 = L / N1;
     constexpr int C = fft_cols(L);
@@ -146,18 +150,46 @@ __device__ __forceinline__ void column_fft_reg_body(const ColumnFFT &a, int bx, 
     // step 1: loads (zero outside the occupied window); all L rows are input
     // rows here (n_in = L), so row r = (f - in_shift) mod L and the window
     // test is (r - wlo) mod L < wlen
-    float2 v[IT1][N1];
+    constexpr int IP = PAIR ? IT1 / 2 : 1;   // column pairs per thread
+    static_assert(!PAIR || (IT1 % 2 == 0 && C % 2 == 0), "pairs of step-1 columns");
+    float2 v[PAIR ? 1 : IT1][N1];
+    cpair vp[IP][PAIR ? N1 : 1];
+    if constexpr (PAIR) {
 #pragma unroll
-    for (int it = 0; it < IT1; ++it) {
-        const int item = tid + it * kFftThreads;
-        const int c = item % C, n2 = item / C;
-        const int r0 = n2 - a.in_shift, d0 = r0 - wlo;
-        const bool cok = c < cw;
+        for (int it = 0; it < IP; ++it) {
+            const int item = tid + it * kFftThreads;
+            const int c = 2 * (item % (C / 2)), n2 = item / (C / 2);
+            const int r0 = n2 - a.in_shift, d0 = r0 - wlo;
+            const bool c0ok = c < cw, c1ok = c + 1 < cw;
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-            const int r = (r0 + N2 * n1) & (L - 1);
-            const bool live = cok && ((d0 + N2 * n1) & (L - 1)) < wlen;
-            v[it][n1] = live ? in[(long long)r * a.in_row + c] : make_float2(0.f, 0.f);
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int r = (r0 + N2 * n1) & (L - 1);
+                const bool live = ((d0 + N2 * n1) & (L - 1)) < wlen;
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 *src = in + (long long)r * a.in_row + c;
+                if (live && c1ok) {
+                    t = __ldg(reinterpret_cast<const float4 *>(src));
+                } else if (live && c0ok) {
+                    const float2 t0 = __ldg(src);
+                    t.x = t0.x;
+                    t.y = t0.y;
+                }
+                vp[it][n1] = cpair{make_float2(t.x, t.z), make_float2(t.y, t.w)};
+            }
+        }
+    } else {
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) {
+            const int item = tid + it * kFftThreads;
+            const int c = item % C, n2 = item / C;
+            const int r0 = n2 - a.in_shift, d0 = r0 - wlo;
+            const bool cok = c < cw;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int r = (r0 + N2 * n1) & (L - 1);
+                const bool live = cok && ((d0 + N2 * n1) & (L - 1)) < wlen;
+                v[it][n1] = live ? in[(long long)r * a.in_row + c] : make_float2(0.f, 0.f);
+            }
         }
     }
     fill_twiddles<L, SIGN>(tw, tid, kFftThreads);
@@ -168,14 +200,32 @@ __device__ __forceinline__ void column_fft_reg_body(const ColumnFFT &a, int bx, 
         dscale[o] = a.gauss_tau > 0.f ? a.scale * expf((float)(f * f) * a.gauss_tau) : a.scale;
     }
     __syncthreads();
+    if constexpr (PAIR) {
 #pragma unroll
-    for (int it = 0; it < IT1; ++it) {
-        const int item = tid + it * kFftThreads;
-        const int c = item % C, n2 = item / C;
-        reg_dft<N1, SIGN>(v[it]);
+        for (int it = 0; it < IP; ++it) {
+            const int item = tid + it * kFftThreads;
+            const int c = 2 * (item % (C / 2)), n2 = item / (C / 2);
+            preg_dft<N1, SIGN>(vp[it]);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1)
-            y[n2 * YP + k1 * C + c] = k1 == 0 ? v[it][0] : cmul(v[it][k1], tw[(n2 * k1) & (L - 1)]);
+            for (int k1 = 0; k1 < N1; ++k1) {
+                cpair o = vp[it][k1];
+                if (k1 > 0) {
+                    const float2 w = tw[(n2 * k1) & (L - 1)];
+                    o = pmul_cs(o, w.x, w.y);
+                }
+                *reinterpret_cast<float4 *>(y + n2 * YP + k1 * C + c) = make_float4(o.re.x, o.im.x, o.re.y, o.im.y);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int it = 0; it < IT1; ++it) {
+            const int item = tid + it * kFftThreads;
+            const int c = item % C, n2 = item / C;
+            reg_dft<N1, SIGN>(v[it]);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                y[n2 * YP + k1 * C + c] = k1 == 0 ? v[it][0] : cmul(v[it][k1], tw[(n2 * k1) & (L - 1)]);
+        }
     }
     __syncthreads();
 
@@ -207,10 +257,10 @@ __global__ void __launch_bounds__(kFftThreads) column_fft_kernel(const __grid_co
     column_fft_body<L, SIGN, VEC>(a, blockIdx.x, blockIdx.y);
 }
 // three CTAs per SM, as the tiles' shared memory allows
-template <int L, int SIGN>
+template <int L, int SIGN, bool PAIR>
 __global__ void __launch_bounds__(kFftThreads, 3)
     column_fft_reg_kernel(const __grid_constant__ ColumnFFT a) {
-    column_fft_reg_body<L, SIGN>(a, blockIdx.x, blockIdx.y);
+    column_fft_reg_body<L, SIGN, PAIR>(a, blockIdx.x, blockIdx.y);
 }
 
 // Fused launches: the tiles of every scan on a 1-D grid (x fastest as above).
@@ -223,26 +273,28 @@ __global__ void __launch_bounds__(kFftThreads)
     const int gx = sa.nt2 * ((sa.ncols + fft_cols(L) - 1) / fft_cols(L));
     column_fft_body<L, SIGN, VEC>(sa, bid % gx, bid / gx);
 }
-template <int L, int SIGN>
+template <int L, int SIGN, bool PAIR>
 __global__ void __launch_bounds__(kFftThreads, 3)
     column_fft_reg_multi(const __grid_constant__ BatchTable<ColumnFFT> t) {
     __shared__ ColumnFFT sa;
     int bid, nb;
     batch_args(t, batch_scan(t, bid, nb), &sa);
     const int gx = sa.nt2 * ((sa.ncols + fft_cols(L) - 1) / fft_cols(L));
-    column_fft_reg_body<L, SIGN>(sa, bid % gx, bid / gx);
+    column_fft_reg_body<L, SIGN, PAIR>(sa, bid % gx, bid / gx);
 }
 
-// Kernel instance of a transform: bit 0-1 the kind (0 register kernel,
-// 1 / 2 the shared-memory kernel with 8- / 16-byte copies), bits 2.. L,
-// bit 20 the inverse sign.
+// Kernel instance of a transform: bit 0-1 the kind (0 / 3 the register
+// kernel, 3 with step 1 on column pairs; 1 / 2 the shared-memory kernel with
+// 8- / 16-byte copies), bits 2.. L, bit 20 the inverse sign.
 static int fft_key(const ColumnFFT &a) {
     const bool reg = a.n_in == a.L && a.L >= 64 && a.L <= 1024;
     // 16-byte copies need every row start (and the column chunk starts) on a
     // 16-byte boundary
     const bool even = (a.ncols % 2 == 0) && (a.in_row % 2 == 0) && (a.in_t1 % 2 == 0) && (a.in_t2 % 2 == 0) &&
                       (reinterpret_cast<uintptr_t>(a.in) % 16 == 0);
-    return (a.sign > 0 ? 1 << 20 : 0) | (a.L << 2) | (reg ? 0 : (even ? 2 : 1));
+    // column pairs in step 1 where every thread takes two step-1 columns
+    const bool pair = reg && even && a.L >= 128 && a.L <= 512;
+    return (a.sign > 0 ? 1 << 20 : 0) | (a.L << 2) | (reg ? (pair ? 3 : 0) : (even ? 2 : 1));
 }
 
 static int fft_blocks(const ColumnFFT &a) {
@@ -251,20 +303,20 @@ static int fft_blocks(const ColumnFFT &a) {
     return a.nt1 * a.nt2 * ((a.ncols + C - 1) / C);
 }
 
-template <int L, int SIGN>
+template <int L, int SIGN, bool PAIR>
 static cudaError_t launch_reg(const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks, cudaStream_t s) {
     constexpr int C = fft_cols(L);
     const size_t smem = (size_t)((L / reg_fft_n1(L)) * reg_fft_pitch(L) + L) * sizeof(float2) + L * sizeof(float);
     if (a) {
-        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN>, smem);
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_kernel<L, SIGN, PAIR>, smem);
         if (e != cudaSuccess) return e;
         const int nchunks = (a->ncols + C - 1) / C;
         dim3 grid((unsigned)(a->nt2 * nchunks), (unsigned)a->nt1);
-        column_fft_reg_kernel<L, SIGN><<<grid, kFftThreads, smem, s>>>(*a);
+        column_fft_reg_kernel<L, SIGN, PAIR><<<grid, kFftThreads, smem, s>>>(*a);
     } else {
-        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_multi<L, SIGN>, smem);
+        cudaError_t e = ensure_smem_attr((const void *)column_fft_reg_multi<L, SIGN, PAIR>, smem);
         if (e != cudaSuccess) return e;
-        column_fft_reg_multi<L, SIGN><<<blocks, kFftThreads, smem, s>>>(*t);
+        column_fft_reg_multi<L, SIGN, PAIR><<<blocks, kFftThreads, smem, s>>>(*t);
     }
     return cudaGetLastError();
 }
@@ -290,8 +342,10 @@ static cudaError_t launch_LV(const ColumnFFT *a, const BatchTable<ColumnFFT> *t,
 template <int L, int SIGN>
 static cudaError_t launch_kind(int kind, const ColumnFFT *a, const BatchTable<ColumnFFT> *t, int blocks,
                                cudaStream_t s) {
+    if constexpr (L >= 128 && L <= 512)
+        if (kind == 3) return launch_reg<L, SIGN, true>(a, t, blocks, s);
     if constexpr (L >= 64 && L <= 1024)
-        if (kind == 0) return launch_reg<L, SIGN>(a, t, blocks, s);
+        if (kind == 0) return launch_reg<L, SIGN, false>(a, t, blocks, s);
     return kind == 2 ? launch_LV<L, SIGN, 2>(a, t, blocks, s) : launch_LV<L, SIGN, 1>(a, t, blocks, s);
 }
 
