@@ -90,6 +90,27 @@ def test_fused_batch_beyond_one_table(dev):
         assert np.array_equal(j.vol.cpu().numpy().view(np.uint32), ref.view(np.uint32))
 
 
+def test_fused_batch_with_empty_and_single_sample_scans(dev):
+    """A scan without samples gets a zero volume (and no fused launch), a
+    one-position scan its own image, next to ordinary scans in one batch."""
+    from paper_2305_02064_gb300.batch import ScanJob, image_batch_fused
+    empty = synth.custom(nx_pos=0, ny_pos=0, nk=8, nx=8, ny=8, nz=4, seed=1)
+    single = synth.custom(nx_pos=1, ny_pos=1, nk=16, layout="tiny", nx=16, ny=16, nz=8, seed=2,
+                          scatterers=[[0.0, 0.0, 0.28, 1.0]])
+    scans = [empty, single] + small_mix(3)
+    jobs = [ScanJob(s, dev) for s in scans]
+    ref = []
+    for j in jobs:
+        j.image()
+        ref.append(j.vol.cpu().numpy())
+        j.vol.fill_(1.0)
+    image_batch_fused(jobs)
+    torch.cuda.synchronize()
+    assert np.all(jobs[0].vol.cpu().numpy() == 0)
+    for j, r in zip(jobs[1:], ref[1:]):
+        assert np.array_equal(j.vol.cpu().numpy().view(np.uint32), r.view(np.uint32))
+
+
 def test_fused_graph_replay_equals_eager(dev):
     from paper_2305_02064_gb300.batch import BatchGraph, ScanJob
     scans = small_mix(5)
