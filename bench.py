@@ -649,6 +649,7 @@ def run_serve(args, dist):
     results = {}
     for name, dtype, slots in (("served_f16", "f16", 8), ("plain_fp32", "c64", 1)):
         ex = GpuExecutor(dev, dtype=dtype, n_streams=slots)
+        ex.reserve(pool)   # every slot's device buffers sized for the largest scan of the mix
         # page-locked inputs once per distinct scan, shared by its requests
         pinned = []
         for sc in pool:

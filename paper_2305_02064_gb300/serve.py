@@ -11,7 +11,9 @@ The scheduling logic (``Scheduler``) is independent of CUDA: it drives an
 executor object with ``start(req) -> handle``, ``done(handle) -> bool`` and
 ``finish(handle)``; ``GpuExecutor`` is the CUDA one (pinned host echo ->
 device on the request's stream, FP16/BF16 quantisation with a per-scan scale,
-imaging, completion event).  Tests drive the scheduler with a fake executor.
+imaging, completion event; each stream slot reuses its own device buffers, so
+steady-state serving allocates no device memory).  Tests drive the scheduler
+with a fake executor.
 """
 from __future__ import annotations
 
@@ -125,6 +127,10 @@ class GpuExecutor:
         self.free_streams = list(range(n_streams))
         self.keep = keep_results
         self._out_pool = collections.defaultdict(list)   # volume shape -> free pinned volumes
+        # per slot: device buffers reused by every request the slot serves
+        # (grown to the largest request seen, or sized up front by reserve):
+        # no device allocation in steady state, so no allocator stall
+        self._slot_bufs = [{} for _ in range(n_streams)]
 
     def footprint(self, scan):
         from .batch import plan_for
@@ -142,6 +148,38 @@ class GpuExecutor:
         req.pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                       for a in (s.echo, np.asarray(s.pos, np.float64), np.asarray(s.tx, np.float64),
                                 np.asarray(s.rx, np.float64))]
+
+    def _sizes(self, scan):
+        from .batch import plan_for
+        p = plan_for(scan, dtype=self.dtype)
+        T, R, P, Nk = scan.echo.shape
+        g = scan.grid
+        return {"echo": (T * R * P * Nk, "c64"), "q": (T * R * P * Nk * 2, self.dtype),
+                "geo": (3 * (P + T + R), "f64"), "ws": (p.workspace_bytes, "u8"), "vol": (g.nx * g.ny * g.nz, "c64")}
+
+    def _take(self, si, name, numel, kind):
+        import torch
+        dt = {"c64": torch.complex64, "f16": torch.float16, "bf16": torch.bfloat16, "f64": torch.float64,
+              "u8": torch.uint8, "f32": torch.float32, "i32": torch.int32}[kind]
+        bufs = self._slot_bufs[si]
+        t = bufs.get(name)
+        if t is None or t.numel() < numel:
+            with torch.cuda.stream(self.streams[si]):
+                t = torch.empty(max(numel, 1), dtype=dt, device=self.dev)
+            bufs[name] = t
+        return t[:numel]
+
+    def reserve(self, scans):
+        """Size every slot's buffers for the largest of ``scans`` (before serving)."""
+        need = {}
+        for sc in scans:
+            for name, (n, kind) in self._sizes(sc).items():
+                need[name] = (max(n, need.get(name, (0, kind))[0]), kind)
+        for si in range(len(self.streams)):
+            for name, (n, kind) in need.items():
+                if name == "q" and self.dtype == "c64":
+                    continue
+                self._take(si, name, n, kind)
 
     def _out_buffer(self, shape):
         import torch
@@ -161,14 +199,22 @@ class GpuExecutor:
             self.pin(req)
         echo_h, pos_h, tx_h, rx_h = req.pinned
         vol_h = self._out_buffer(plan.volume_shape)
+        sz = self._sizes(req.scan)
+        echo = self._take(si, "echo", *sz["echo"]).view(echo_h.shape)
+        geo = self._take(si, "geo", *sz["geo"])
+        ws = self._take(si, "ws", *sz["ws"])
+        vol = self._take(si, "vol", *sz["vol"]).view(plan.volume_shape)
         with torch.cuda.stream(st):
-            echo = echo_h.to(self.dev, non_blocking=True)
-            pos, tx, rx = (t.to(self.dev, non_blocking=True) for t in (pos_h, tx_h, rx_h))
+            echo.copy_(echo_h, non_blocking=True)
+            pos, tx, rx = (geo[o:o + t.numel()].view(t.shape) for o, t in
+                           zip((0, pos_h.numel(), pos_h.numel() + tx_h.numel()), (pos_h, tx_h, rx_h)))
+            for d, h in zip((pos, tx, rx), (pos_h, tx_h, rx_h)):
+                d.copy_(h, non_blocking=True)
             scale = None
             if self.dtype != "c64":
-                echo, scale = quantize_echo(echo, self.dtype, stream=st)
-            ws = plan.new_workspace(self.dev)
-            vol = plan.new_volume(self.dev)
+                out = self._take(si, "q", *sz["q"]).view(tuple(echo.shape) + (2,))
+                echo, scale = quantize_echo(echo, self.dtype, out=out, scale=self._take(si, "scale", 1, "f32"),
+                                            scratch=self._take(si, "scratch", 1, "i32"), stream=st)
             plan.image(ws, echo, pos, tx, rx, vol, echo_scale=scale, stream=st)
             vol_h.copy_(vol, non_blocking=True)
             ev = torch.cuda.Event()
