@@ -10,9 +10,10 @@ latency runs from its arrival to the completion of its volume.
 The scheduling logic (``Scheduler``) is independent of CUDA: it drives an
 executor object with ``start(req) -> handle``, ``done(handle) -> bool`` and
 ``finish(handle)``; ``GpuExecutor`` is the CUDA one (pinned host echo ->
-device on the request's stream, FP16/BF16 quantisation with a per-scan scale,
-imaging, completion event; each stream slot reuses its own device buffers, so
-steady-state serving allocates no device memory).  Tests drive the scheduler
+device on the request's stream -- for FP16/BF16 storage the echo is kept as
+scaled pairs, quantised once per scan on the device --, imaging, completion
+event; each stream slot reuses its own device buffers, so steady-state
+serving allocates no device memory).  Tests drive the scheduler
 with a fake executor.
 """
 from __future__ import annotations
@@ -136,26 +137,43 @@ class GpuExecutor:
         from .batch import plan_for
         p = plan_for(scan, dtype=self.dtype)
         T, R, P, Nk = scan.echo.shape
-        echo_dev = T * R * P * Nk * (8 if self.dtype == "c64" else 4)
-        staging = T * R * P * Nk * 8 if self.dtype != "c64" else 0
+        echo_dev = T * R * P * Nk * (8 if self.dtype == "c64" else 4)   # complex64, or FP16/BF16 pairs
         g = scan.grid
-        return int(p.workspace_bytes + echo_dev + staging + 8 * g.nx * g.ny * g.nz + 48 * (P + T + R))
+        return int(p.workspace_bytes + echo_dev + 8 * g.nx * g.ny * g.nz + 48 * (P + T + R))
 
     def pin(self, req):
+        """Page-locked host copies of a request's inputs.  For FP16/BF16 storage
+        the echo is stored reduced: it goes to the device once, the library's
+        quantisation kernel turns it into scaled pairs, and those (with the
+        scale) come back to pinned host memory -- every request of the scan
+        then moves half the echo bytes."""
         import numpy as np
         import torch
+        from . import quantize_echo
         s = req.scan
-        req.pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                      for a in (s.echo, np.asarray(s.pos, np.float64), np.asarray(s.tx, np.float64),
-                                np.asarray(s.rx, np.float64))]
+        geo = [torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory() for a in (s.pos, s.tx, s.rx)]
+        echo_h = torch.from_numpy(np.ascontiguousarray(s.echo)).pin_memory()
+        if self.dtype == "c64":
+            req.pinned = [echo_h, None] + geo
+            return
+        st = self.streams[0]
+        with torch.cuda.stream(st):
+            q, scale = quantize_echo(echo_h.to(self.dev, non_blocking=True), self.dtype, stream=st)
+            q_h = torch.empty(q.shape, dtype=q.dtype).pin_memory()
+            scale_h = torch.empty(1, dtype=torch.float32).pin_memory()
+            q_h.copy_(q, non_blocking=True)
+            scale_h.copy_(scale, non_blocking=True)
+        st.synchronize()
+        req.pinned = [q_h, scale_h] + geo
 
     def _sizes(self, scan):
         from .batch import plan_for
         p = plan_for(scan, dtype=self.dtype)
         T, R, P, Nk = scan.echo.shape
         g = scan.grid
-        return {"echo": (T * R * P * Nk, "c64"), "q": (T * R * P * Nk * 2, self.dtype),
-                "geo": (3 * (P + T + R), "f64"), "ws": (p.workspace_bytes, "u8"), "vol": (g.nx * g.ny * g.nz, "c64")}
+        echo = (T * R * P * Nk, "c64") if self.dtype == "c64" else (T * R * P * Nk * 2, self.dtype)
+        return {"echo": echo, "geo": (3 * (P + T + R), "f64"), "ws": (p.workspace_bytes, "u8"),
+                "vol": (g.nx * g.ny * g.nz, "c64")}
 
     def _take(self, si, name, numel, kind):
         import torch
@@ -177,9 +195,8 @@ class GpuExecutor:
                 need[name] = (max(n, need.get(name, (0, kind))[0]), kind)
         for si in range(len(self.streams)):
             for name, (n, kind) in need.items():
-                if name == "q" and self.dtype == "c64":
-                    continue
                 self._take(si, name, n, kind)
+            self._take(si, "scale", 1, "f32")
 
     def _out_buffer(self, shape):
         import torch
@@ -190,31 +207,28 @@ class GpuExecutor:
 
     def start(self, req):
         import torch
-        from . import quantize_echo
         from .batch import plan_for
         si = self.free_streams.pop()
         st = self.streams[si]
         plan = plan_for(req.scan, dtype=self.dtype)
         if req.pinned is None:
             self.pin(req)
-        echo_h, pos_h, tx_h, rx_h = req.pinned
+        echo_h, scale_h, pos_h, tx_h, rx_h = req.pinned
         vol_h = self._out_buffer(plan.volume_shape)
         sz = self._sizes(req.scan)
         echo = self._take(si, "echo", *sz["echo"]).view(echo_h.shape)
         geo = self._take(si, "geo", *sz["geo"])
         ws = self._take(si, "ws", *sz["ws"])
         vol = self._take(si, "vol", *sz["vol"]).view(plan.volume_shape)
+        scale = None if scale_h is None else self._take(si, "scale", 1, "f32")
         with torch.cuda.stream(st):
             echo.copy_(echo_h, non_blocking=True)
+            if scale is not None:
+                scale.copy_(scale_h, non_blocking=True)
             pos, tx, rx = (geo[o:o + t.numel()].view(t.shape) for o, t in
                            zip((0, pos_h.numel(), pos_h.numel() + tx_h.numel()), (pos_h, tx_h, rx_h)))
             for d, h in zip((pos, tx, rx), (pos_h, tx_h, rx_h)):
                 d.copy_(h, non_blocking=True)
-            scale = None
-            if self.dtype != "c64":
-                out = self._take(si, "q", *sz["q"]).view(tuple(echo.shape) + (2,))
-                echo, scale = quantize_echo(echo, self.dtype, out=out, scale=self._take(si, "scale", 1, "f32"),
-                                            scratch=self._take(si, "scratch", 1, "i32"), stream=st)
             plan.image(ws, echo, pos, tx, rx, vol, echo_scale=scale, stream=st)
             vol_h.copy_(vol, non_blocking=True)
             ev = torch.cuda.Event()
