@@ -180,6 +180,8 @@ inline thread_local int g_fused_launches = 0;
 
 template <typename A, typename K, typename F>
 cudaError_t launch_groups(int n, const K *keys, const A *args, const int *blocks, F fn) {
+    // kernel parameters may take up to 32 KB (CUDA 12.1+); stay well inside
+    static_assert(sizeof(BatchTable<A>) <= 16384, "fused-launch argument table too large");
     std::vector<char> done((size_t)n, 0);
     for (int i = 0; i < n; ++i) {
         if (done[i] || blocks[i] <= 0) continue;
