@@ -62,8 +62,12 @@ constexpr int kListCap = 192;   // relevant samples listed per warp before they 
 template <int NF, int WARPS, int NS, int MINB>
 __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     constexpr int TX = 4 * (WARPS / 2);   // tile width in cells (two block rows)
-    // per warp: (x-quad index, y-quad index, sample index) of each listed sample
-    __shared__ int4 lists[WARPS][kListCap];
+    // per warp and listed sample: its x and y weight quads (gathered from the
+    // records while the list is built, one lane per sample) and its index;
+    // eight warps list fewer samples at a time (static shared memory <= 48 KB)
+    constexpr int CAP = WARPS == 8 ? 160 : kListCap;
+    __shared__ float4 lquads[WARPS][CAP][2];
+    __shared__ int lidx[WARPS][CAP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tiles_x = a.mrx / TX;
     // the frequency group varies fastest, so the groups of one tile run
@@ -91,11 +95,11 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     // are 8 NF contiguous bytes at row offset (sample * 64 + col0) complex
     const int col0 = NF == 2 ? 2 * lane : (kg & 1) * 32 + lane;
     const float2 *sh = a.shat + (long long)(NF == 2 ? kg : kg >> 1) * a.Lmax * 64 + col0;
-    int4 *list = lists[warp];
+    float4 (*quads)[2] = lquads[warp];
+    int *sidx = lidx[warp];
 
-    // one listed sample in flight: its x and y weight quads and its values
+    // one listed sample in flight: its values (the weights wait in shared memory)
     struct Stage {
-        float4 x, y;
         float2 v[NF];
     };
     // apply the listed samples through an NS-deep pipeline: the loads of
@@ -103,21 +107,20 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     auto apply = [&](int n) {
         Stage st[NS];
         auto fetch = [&](int i, Stage &q) {
-            const int4 e = list[i];
-            q.x = __ldg(a.wrec + e.x);
-            q.y = __ldg(a.wrec + e.y);
+            const int l = sidx[i];
             if constexpr (NF == 2) {
                 // sample index * 32 < 2^31 (plan limit): 32-bit offsets in float4 units
-                const float4 t = __ldg(reinterpret_cast<const float4 *>(sh) + (e.z << 5));
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(sh) + (l << 5));
                 q.v[0] = make_float2(t.x, t.y);
                 q.v[NF - 1] = make_float2(t.z, t.w);
             } else {
-                q.v[0] = __ldg(sh + ((long long)e.z << 6));
+                q.v[0] = __ldg(sh + ((long long)l << 6));
             }
         };
-        auto consume = [&](const Stage &q) {
-            const float wx[4] = {q.x.x, q.x.y, q.x.z, q.x.w};
-            const float wy[4] = {q.y.x, q.y.y, q.y.z, q.y.w};
+        auto consume = [&](int i, const Stage &q) {
+            const float4 qx = quads[i][0], qy = quads[i][1];
+            const float wx[4] = {qx.x, qx.y, qx.z, qx.w};
+            const float wy[4] = {qy.x, qy.y, qy.z, qy.w};
             // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -137,7 +140,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
 #pragma unroll
             for (int k = 0; k < NS; ++k) {
                 if (i + k >= n) break;
-                consume(st[k]);
+                consume(i + k, st[k]);
                 if (i + k + NS < n) fetch(i + k + NS, st[k]);
             }
         }
@@ -169,13 +172,18 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
                     ent = make_int4(base + ru + 3, base + nq + rv + 3, ds.y, 0);
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, rel);
-                if (n + __popc(mask) > kListCap) {   // keep the list within its buffer
+                if (n + __popc(mask) > CAP) {   // keep the list within its buffer
                     __syncwarp();
                     apply(n);
                     n = 0;
                     __syncwarp();
                 }
-                if (rel) list[n + __popc(mask & lt)] = ent;
+                if (rel) {
+                    const int pos = n + __popc(mask & lt);
+                    quads[pos][0] = __ldg(a.wrec + ent.x);
+                    quads[pos][1] = __ldg(a.wrec + ent.y);
+                    sidx[pos] = ent.z;
+                }
                 n += __popc(mask);
             }
         }
@@ -250,17 +258,18 @@ static void spread_launch(const SpreadArgs *a, const BatchTable<SpreadArgs> *t, 
 static void spread_dispatch(int key, const SpreadArgs *a, const BatchTable<SpreadArgs> *t, int blocks,
                             cudaStream_t s) {
     switch (key) {
-        case 5: spread_launch<2, 8, 3, 2>(a, t, blocks, s); break;
-        case 4: spread_launch<2, 4, 3, 4>(a, t, blocks, s); break;
-        case 3: spread_launch<1, 8, 3, 3>(a, t, blocks, s); break;
-        default: spread_launch<1, 4, 3, 6>(a, t, blocks, s); break;
+        case 5: spread_launch<2, 8, 8, 2>(a, t, blocks, s); break;
+        case 4: spread_launch<2, 4, 8, 4>(a, t, blocks, s); break;
+        case 3: spread_launch<1, 8, 8, 2>(a, t, blocks, s); break;
+        default: spread_launch<1, 4, 8, 5>(a, t, blocks, s); break;
     }
 }
 
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     // the launch shape is the plan's (set by mmsar_plan_set_tiles, e.g. from
-    // the autotuner): NF frequencies per lane, WARPS warps per CTA; three
-    // listed samples in flight
+    // the autotuner): NF frequencies per lane, WARPS warps per CTA; eight
+    // listed samples in flight (only their compensated values sit in
+    // registers: the weights wait in the shared-memory list)
     SpreadArgs a;
     const int blocks = spread_describe(p, ws, a);
     spread_dispatch(2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0), &a, nullptr, blocks, s);
