@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default gridding launch shape")
+    ap.add_argument("--tiles", default=None,
+                    help="gridding launch shape 'nf,warps,grouped' instead of the autotuner's (single-scan workloads)")
     return ap.parse_args()
 
 
@@ -306,7 +308,9 @@ def run_ours(args, dist):
     torch.cuda.synchronize(dev)
     # the autotuner picks the gridding launch shape on this scan (untimed)
     tuned = None
-    if not args.no_autotune:
+    if args.tiles:
+        plan.set_tiles(*(int(v) for v in args.tiles.split(",")))
+    elif not args.no_autotune:
         from paper_2305_02064_gb300.tune import autotune
         tuned = autotune(plan, ws, echo, pos, tx, rx, vol, stream=stream)
         torch.cuda.synchronize(dev)

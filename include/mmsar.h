@@ -121,8 +121,11 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
  * scan (small scans fill the GPU better with smaller CTAs; arrays whose Tx
  * and Rx lie on one line along y give large groups).  Defaults: 2, 4, 0. */
 typedef struct {
-    int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64           */
-    int grid_warps_per_cta;    /* 4: an 8 x 8-cell tile; 8: a 16 x 8-cell tile     */
+    int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64; 4: 128,   *
+                                * in 4 x 2-cell warp blocks (fewer taps outside   *
+                                * the support; per-sample form only)              */
+    int grid_warps_per_cta;    /* 4: an 8 x 8-cell tile (8 x 4 for 4 frequencies  *
+                                * per lane); 8: 16 x 8 (16 x 4)                   */
     int grid_grouped;          /* 1: the samples of one position whose Tx/Rx pairs *
                                 * share the x offset (Eq. 3: the same x') are     *
                                 * gridded together, the x weights applied once to *

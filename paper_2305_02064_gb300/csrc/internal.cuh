@@ -78,8 +78,8 @@ struct Plan {
     int nkp;            // n_kc * 32
     int64_t L;          // n_tx n_rx n_pos
     int nbx, nby;       // bins per axis (mrx / 4, mry / 4)
-    int spread_nf;      // gridding launch shape: frequencies per lane (1 or 2)
-    int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells)
+    int spread_nf;      // gridding launch shape: frequencies per lane (1, 2 or 4)
+    int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells; half as tall for 4)
     bool grouped;       // gridding by groups of samples sharing x' (else per sample)
     int64_t G;          // group slots: n_tx n_rx n_pos (every class may be a single pair)
     int64_t n_bins;

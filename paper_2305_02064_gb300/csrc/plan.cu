@@ -273,12 +273,14 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
 
 mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
     if (!plan || !tiles) return fail(MMSAR_ERR_INVALID_ARG, "null plan or tiles");
-    if (tiles->grid_freqs_per_lane != 1 && tiles->grid_freqs_per_lane != 2)
-        return fail(MMSAR_ERR_INVALID_ARG, "grid_freqs_per_lane must be 1 or 2");
+    if (tiles->grid_freqs_per_lane != 1 && tiles->grid_freqs_per_lane != 2 && tiles->grid_freqs_per_lane != 4)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_freqs_per_lane must be 1, 2 or 4");
     if (tiles->grid_warps_per_cta != 4 && tiles->grid_warps_per_cta != 8)
         return fail(MMSAR_ERR_INVALID_ARG, "grid_warps_per_cta must be 4 or 8");
     if (tiles->grid_grouped != 0 && tiles->grid_grouped != 1)
         return fail(MMSAR_ERR_INVALID_ARG, "grid_grouped must be 0 or 1");
+    if (tiles->grid_grouped && tiles->grid_freqs_per_lane == 4)
+        return fail(MMSAR_ERR_INVALID_ARG, "the grouped form takes 1 or 2 frequencies per lane");
     if (tiles->grid_grouped && (int64_t)plan->p.shape.n_tx * plan->p.shape.n_rx > kMaxPairsGrouped)
         return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "grouped gridding takes at most %d Tx/Rx pairs", kMaxPairsGrouped);
     plan->p.spread_nf = tiles->grid_freqs_per_lane;

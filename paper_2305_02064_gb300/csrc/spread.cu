@@ -14,18 +14,20 @@
 // block needs when it starts q - 3 cells after u0.  The compensated samples
 // are in original sample order.
 //
-// spread_kernel: a CTA owns a 16x8 tile of grid cells and two chunks of 32
-// frequencies; each of its 8 warps owns a 4x4 block of cells, and each lane
-// keeps in registers the 16 complex accumulators of its frequency in both
-// chunks (the per-sample list entry, weight loads and loop control are shared
-// by the two).  Warps work independently (no block barrier): a warp walks the
-// bins whose samples can reach its block, tests 32 samples at a time (one lane
-// each) for overlap with the block and appends the overlapping ones to a list
-// in shared memory, then applies the list with the loads of the next three
-// entries in flight.  For a bin d bins before the block, the block starts
-// 4 d - (in-bin offset) cells after the sample's first tap, which selects one
-// weight quad per axis (two 16-byte broadcast loads).  No two warps write the
-// same cell: no atomics, a fixed summation order.
+// spread_kernel: a CTA owns a tile of grid cells and a group of frequency
+// chunks; each of its warps owns a block of cells (4 x 4, or 4 x 2 when a lane
+// keeps four frequencies), and each lane keeps in registers the complex
+// accumulators of its frequencies over the block.  Warps work independently
+// (no block barrier): a warp walks the bins whose samples can reach its block,
+// tests 32 samples at a time (one lane each) for overlap with the block and
+// appends the overlapping ones to a list in shared memory -- the sample index
+// and, gathered from the records, the two weight quads its position in the
+// block selects -- then applies the list with the compensated values of the
+// next few entries in flight.  For a bin d bins before the block, the block
+// starts 4 d - (in-bin offset) cells after the sample's first tap (plus the
+// block's own offset inside its bin), which selects one weight quad per axis.
+// No two warps write the same cell: no atomics, a fixed summation order, the
+// same for every launch shape (so all shapes give the same bits).
 #include "fft.cuh"
 #include "internal.cuh"
 
@@ -57,11 +59,16 @@ __device__ __forceinline__ bool tile_meets(int t0, int span, int lo, int len, in
 constexpr int kListCap = 192;   // relevant samples listed per warp before they are applied
 
 // NF: frequencies per lane (1: a CTA covers one chunk of 32 frequencies; 2:
-// a 64-frequency group, lane l holding frequencies 2l and 2l + 1); WARPS: 8
-// (a 16 x 8-cell tile) or 4 (8 x 8 cells), each warp a 4 x 4-cell block.
+// a 64-frequency group, lane l holding frequencies 2l and 2l + 1; 4: a
+// 128-frequency group, lane l holding 4l .. 4l + 3); WARPS: 4 or 8, in two
+// block rows.  Warp blocks are 4 x 4 cells, or 4 x 2 for NF = 4 (the same
+// accumulator count per lane; fewer taps outside the sample's support:
+// (w + 3)(w + 1) cells visited per sample instead of (w + 3)^2).
 template <int NF, int WARPS, int NS, int MINB>
 __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
+    constexpr int BY = NF == 4 ? 2 : 4;   // block rows (cells along y')
     constexpr int TX = 4 * (WARPS / 2);   // tile width in cells (two block rows)
+    constexpr int TY = 2 * BY;
     // per warp and listed sample: its x and y weight quads (gathered from the
     // records while the list is built, one lane per sample) and its index;
     // eight warps list fewer samples at a time (static shared memory <= 48 KB)
@@ -72,29 +79,33 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     const int tiles_x = a.mrx / TX;
     // the frequency group varies fastest, so the groups of one tile run
     // together and share its weight records in L2
-    const int n_kg = NF == 2 ? (a.n_kc + 1) / 2 : a.n_kc;
+    const int n_kg = (a.n_kc + NF - 1) / NF;
     const int kg = bid % n_kg;
     const int tile = bid / n_kg;
     // tiles outside the occupied window stay unwritten: the FFT along x'
     // reads only the window and takes the rest as zero
     if (!tile_meets((tile % tiles_x) * TX, TX, a.hdr->u_lo, a.hdr->u_len, a.mrx) ||
-        !tile_meets((tile / tiles_x) * 8, 8, a.hdr->v_lo, a.hdr->v_len, a.mry))
+        !tile_meets((tile / tiles_x) * TY, TY, a.hdr->v_lo, a.hdr->v_len, a.mry))
         return;
     const int U = (tile % tiles_x) * TX + (warp % (WARPS / 2)) * 4;
-    const int V = (tile / tiles_x) * 8 + (warp / (WARPS / 2)) * 4;
+    const int V = (tile / tiles_x) * TY + (warp / (WARPS / 2)) * BY;
     const int rq = 2 * (a.w + 3) + 1;
     const int nq = a.w + 3;
-    float2 acc[NF][4][4];   // (re, im) per frequency of the lane and cell
+    float2 acc[NF][BY][4];   // (re, im) per frequency of the lane and cell
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < BY; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc[f][j][i] = make_float2(0.f, 0.f);
-    // s_hat: [n_kc / 2][Lmax][64] complex; the lane's NF values of a sample
-    // are 8 NF contiguous bytes at row offset (sample * 64 + col0) complex
-    const int col0 = NF == 2 ? 2 * lane : (kg & 1) * 32 + lane;
-    const float2 *sh = a.shat + (long long)(NF == 2 ? kg : kg >> 1) * a.Lmax * 64 + col0;
+    // s_hat: [(n_kc + 1) / 2][Lmax][64] complex; the lane's NF values of a
+    // sample are 8 NF contiguous bytes at row offset (sample * 64 + col0)
+    // complex of 64-frequency group gi (for NF = 4 the upper half-warp reads
+    // the second group, absent when the chunk count leaves it out)
+    const int gi = NF == 4 ? 2 * kg + (lane >> 4) : NF == 2 ? kg : kg >> 1;
+    const int col0 = NF == 4 ? 4 * (lane & 15) : NF == 2 ? 2 * lane : (kg & 1) * 32 + lane;
+    const bool has = NF != 4 || gi < (a.n_kc + 1) / 2;
+    const float2 *sh = a.shat + (long long)(has ? gi : 0) * a.Lmax * 64 + col0;
     float4 (*quads)[2] = lquads[warp];
     int *sidx = lidx[warp];
 
@@ -108,8 +119,19 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
         Stage st[NS];
         auto fetch = [&](int i, Stage &q) {
             const int l = sidx[i];
-            if constexpr (NF == 2) {
+            if constexpr (NF == 4) {
                 // sample index * 32 < 2^31 (plan limit): 32-bit offsets in float4 units
+                float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+                if (has) {
+                    const float4 *p4 = reinterpret_cast<const float4 *>(sh) + (l << 5);
+                    t0 = __ldg(p4);
+                    t1 = __ldg(p4 + 1);
+                }
+                q.v[0] = make_float2(t0.x, t0.y);
+                q.v[1] = make_float2(t0.z, t0.w);
+                q.v[2] = make_float2(t1.x, t1.y);
+                q.v[NF - 1] = make_float2(t1.z, t1.w);
+            } else if constexpr (NF == 2) {
                 const float4 t = __ldg(reinterpret_cast<const float4 *>(sh) + (l << 5));
                 q.v[0] = make_float2(t.x, t.y);
                 q.v[NF - 1] = make_float2(t.z, t.w);
@@ -123,7 +145,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
             const float wy[4] = {qy.x, qy.y, qy.z, qy.w};
             // (re, im) pairs in packed two-lane FP32 instructions
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < BY; ++j) {
                 const float2 wyj = make_float2(wy[j], wy[j]);
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -147,6 +169,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     };
 
     const int bu0 = U >> 2, bv0 = V >> 2;
+    const int v_in = V & 3;   // the block's first row inside its bin (0, or 2 for 4 x 2 blocks)
     const unsigned lt = (1u << lane) - 1u;
     int n = 0;
     for (int dbv = a.nb - 1; dbv >= 0; --dbv) {
@@ -165,10 +188,10 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
                 if (my < end) {
                     const int2 ds = __ldg(a.dd + my);
                     const int d = ds.x;
-                    const int ru = 4 * dbu - (d & 3);     // block start relative to the first tap, >= -3
-                    const int rv = 4 * dbv - (d >> 2);
-                    rel = ru < a.w && rv < a.w;
-                    const int base = my * rq + 1;         // the sample's x quads, then its y quads
+                    const int ru = 4 * dbu - (d & 3);             // block start relative to the first tap, >= -3
+                    const int rv = 4 * dbv - (d >> 2) + v_in;     // >= -3; a 4 x 2 block needs >= -1
+                    rel = ru < a.w && rv < a.w && rv > -BY;
+                    const int base = my * rq + 1;                 // the sample's x quads, then its y quads
                     ent = make_int4(base + ru + 3, base + nq + rv + 3, ds.y, 0);
                 }
                 const unsigned mask = __ballot_sync(0xffffffffu, rel);
@@ -190,14 +213,29 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     }
     __syncwarp();
     apply(n);
-    if constexpr (NF == 2) {
+    if constexpr (NF == 4) {
+        // lane l holds chunk 4 kg + l / 8 (absent past the chunk count),
+        // complex 4 (l % 8) .. + 3 of it: 32 bytes per lane, 256 contiguous bytes per chunk
+        const int kc = 4 * kg + (lane >> 3);
+        if (kc < a.n_kc) {
+            float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + 2 * (lane & 7);
+#pragma unroll
+            for (int j = 0; j < BY; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float4 *c = g + ((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2);
+                    c[0] = make_float4(acc[0][j][i].x, acc[0][j][i].y, acc[1][j][i].x, acc[1][j][i].y);
+                    c[1] = make_float4(acc[2][j][i].x, acc[2][j][i].y, acc[NF - 1][j][i].x, acc[NF - 1][j][i].y);
+                }
+        }
+    } else if constexpr (NF == 2) {
         // lanes 0..15 hold chunk 2 kg, lanes 16..31 chunk 2 kg + 1 (absent when
         // the chunk count is odd): 16 bytes per lane, 256 contiguous bytes per chunk
         const int kc = 2 * kg + (lane >> 4);
         if (kc < a.n_kc) {
             float4 *g = reinterpret_cast<float4 *>(a.G + (long long)kc * a.mry * a.mrx * kKC) + (lane & 15);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < BY; ++j)
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
                     g[((long long)(V + j) * a.mrx + (U + i)) * (kKC / 2)] =
@@ -206,7 +244,7 @@ __device__ __forceinline__ void spread_body(const SpreadArgs &a, int bid) {
     } else {
         float2 *g = a.G + (long long)kg * a.mry * a.mrx * kKC + lane;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < BY; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) g[((long long)(V + j) * a.mrx + (U + i)) * kKC] = acc[0][j][i];
     }
@@ -242,8 +280,8 @@ static int spread_describe(const Plan &p, void *ws, SpreadArgs &a) {
     a.nb = (p.w - 1 + kBin - 1) / kBin + 1;
     a.n_kc = p.n_kc;
     const int nf = p.spread_nf, warps = p.spread_warps;
-    const int tiles = (p.mrx / (2 * warps)) * (p.mry / 8);
-    return tiles * (nf == 2 ? (p.n_kc + 1) / 2 : p.n_kc);
+    const int tiles = (p.mrx / (2 * warps)) * (p.mry / (nf == 4 ? 4 : 8));
+    return tiles * ((p.n_kc + nf - 1) / nf);
 }
 
 template <int NF, int WARPS, int NS, int MINB>
@@ -258,6 +296,8 @@ static void spread_launch(const SpreadArgs *a, const BatchTable<SpreadArgs> *t, 
 static void spread_dispatch(int key, const SpreadArgs *a, const BatchTable<SpreadArgs> *t, int blocks,
                             cudaStream_t s) {
     switch (key) {
+        case 9: spread_launch<4, 8, 4, 2>(a, t, blocks, s); break;
+        case 8: spread_launch<4, 4, 4, 4>(a, t, blocks, s); break;
         case 5: spread_launch<2, 8, 8, 2>(a, t, blocks, s); break;
         case 4: spread_launch<2, 4, 8, 4>(a, t, blocks, s); break;
         case 3: spread_launch<1, 8, 8, 2>(a, t, blocks, s); break;
@@ -267,9 +307,9 @@ static void spread_dispatch(int key, const SpreadArgs *a, const BatchTable<Sprea
 
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s) {
     // the launch shape is the plan's (set by mmsar_plan_set_tiles, e.g. from
-    // the autotuner): NF frequencies per lane, WARPS warps per CTA; eight
-    // listed samples in flight (only their compensated values sit in
-    // registers: the weights wait in the shared-memory list)
+    // the autotuner): NF frequencies per lane, WARPS warps per CTA; 32 bytes
+    // of compensated values per lane in flight (eight listed samples, four
+    // for NF = 4; the weights wait in the shared-memory list)
     SpreadArgs a;
     const int blocks = spread_describe(p, ws, a);
     spread_dispatch(2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0), &a, nullptr, blocks, s);

@@ -3,7 +3,7 @@
 Every shape of ``mmsar_tiles`` computes the same image (the grouped form to
 rounding); which is fastest depends on the scan (a small scan fills the GPU
 better with CTAs over 32 frequencies or 8 x 8-cell tiles, a large one
-prefers 64 frequencies; arrays whose pairs share x offsets gain from the
+prefers 64 or 128 frequencies; arrays whose pairs share x offsets gain from the
 grouped form).  ``autotune`` images the caller's own data with each shape on
 the caller's stream, timed with CUDA events, and leaves the plan set to the
 fastest; the result is kept on the plan, so plans shared by scans of one
@@ -13,7 +13,9 @@ and the images are the library's.
 from __future__ import annotations
 
 # (frequencies per lane, warps per CTA, grouped)
-SHAPES = tuple((nf, wp, gr) for gr in (1, 0) for nf, wp in ((2, 8), (1, 8), (2, 4), (1, 4)))
+# (four frequencies per lane: 4 x 2-cell warp blocks, per-sample form only)
+SHAPES = (tuple((nf, wp, gr) for gr in (1, 0) for nf, wp in ((2, 8), (1, 8), (2, 4), (1, 4)))
+          + ((4, 8, 0), (4, 4, 0)))
 
 
 def autotune(plan, ws, echo, pos, tx, rx, vol, echo_scale=None, stream=None, reps: int = 3,

@@ -314,7 +314,7 @@ def test_gridding_launch_shapes_are_bit_identical(dev):
                         jitter=(0.7e-3, 3e-3), snr_db=25)
     from paper_2305_02064_gb300 import Plan
     vols = {}
-    for shp in ((2, 8), (1, 8), (2, 4), (1, 4)):
+    for shp in ((2, 8), (1, 8), (2, 4), (1, 4), (4, 8), (4, 4)):
         plan = Plan.for_scan(scan)
         plan.set_tiles(*shp)
         ws = plan.new_workspace(dev)
@@ -328,6 +328,32 @@ def test_gridding_launch_shapes_are_bit_identical(dev):
     for shp, v in vols.items():
         assert np.array_equal(v.view(np.uint64), ref.view(np.uint64)), shp
     assert_parity(ref, oracle_of(scan), 6)
+
+
+@pytest.mark.parametrize("nk", [96, 160, 256])
+def test_four_frequency_blocks(dev, nk):
+    """Four frequencies per lane in 4 x 2-cell warp blocks, at 3, 5 and 8
+    frequency chunks (the upper half-warp's 64-frequency group absent, a
+    chunk past the count, full 128-frequency groups), over several CTA tiles
+    with block rows that start inside a bin: bit-identical to the 4 x 4
+    blocks, and within the bound of the oracle."""
+    scan = synth.custom(nx_pos=24, ny_pos=20, nk=nk, layout="awr1443", nx=48, ny=40, nz=12, dz=4e-3, z0=0.26,
+                        seed=31 + nk, serp=True, jitter=(1.5e-3, 3e-3), n_points=4)
+    from paper_2305_02064_gb300 import Plan
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    vols = {}
+    for shp in ((2, 4), (4, 4), (4, 8)):
+        plan = Plan.for_scan(scan)
+        plan.set_tiles(*shp)
+        ws = plan.new_workspace(dev)
+        vol = torch.full(plan.volume_shape, complex(np.nan, np.nan), dtype=torch.complex64, device=dev)
+        plan.image(ws, t(scan.echo), t(np.asarray(scan.pos, np.float64)), t(np.asarray(scan.tx, np.float64)),
+                   t(np.asarray(scan.rx, np.float64)), vol)
+        plan.poll_error(ws)
+        vols[shp] = vol.cpu().numpy()
+    for shp in ((4, 4), (4, 8)):
+        assert np.array_equal(vols[shp].view(np.uint64), vols[(2, 4)].view(np.uint64)), shp
+    assert_parity(vols[(4, 4)], oracle_of(scan, fast=True), plan.kernel_width)
 
 
 @pytest.mark.parametrize("layout", ["awr1443", "3x4", "tiny", "offset_x"])
