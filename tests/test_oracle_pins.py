@@ -358,6 +358,25 @@ def test_fast_oracle_k_slices_add_up(tiny_scan):
     assert rma.nmse(parts, full) < 1e-24
 
 
+@pytest.mark.parametrize("fast", [False, True])
+def test_oracle_is_linear_in_the_echo(fast):
+    """The image is linear in the echo (Eq. 11-16 are all linear in s): the
+    image of a*s1 + b*s2 is a*image(s1) + b*image(s2), for complex a, b and
+    two scenes on the same jittered multi-planar scan."""
+    base = synth.custom(nx_pos=8, ny_pos=7, nk=16, layout="awr1443", nx=16, ny=16, nz=8, seed=12,
+                        jitter=(0.7e-3, 3e-3), scatterers=[[1e-3, -2e-3, 0.29, 1.0]])
+    s2 = synth.echo(base.pos, base.tx, base.rx, base.f0, base.df, base.n_k,
+                    np.array([[-3e-3, 2e-3, 0.28, 0.6], [0.0, 4e-3, 0.30, 0.9]]))
+    a, b = 0.7 - 0.2j, -1.3 + 0.5j
+    e1, e2 = base.echo.astype(np.complex128), s2.astype(np.complex128)   # combine without complex64 rounding
+    img = (lambda e: rma.rma_fast(rma.setup_from(base, echo=e))) if fast else \
+          (lambda e: rma.rma_exact(rma.setup_from(base, echo=e)))
+    lhs = img(a * e1 + b * e2)
+    rhs = a * img(e1) + b * img(e2)
+    assert rma.nmse(lhs, rhs) < 1e-24
+    assert np.linalg.norm(img(e2)) > 0.1 * np.linalg.norm(img(e1))   # the second scene is not negligible
+
+
 def test_compensation_sharpens_jittered_scan():
     """Sec. V: without compensation the multi-planar data defocus (lower peak);
     with it the peak is restored near the back-projection peak."""
