@@ -16,9 +16,15 @@ weak scaling, no collective on the data path); the time is the maximum
 over ranks and ``value`` counts the voxels of all ranks.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
-path has) on the host cores, each step a bounded sample of the same
-workload: the first Nk/8 frequencies of the scan (the image is linear in
-them), scaled to voxels/s.
+path has) on the host cores, each step one whole image of the same scan.
+
+At N = 1 the line also carries the oracle timings on the host cores
+(``oracle_timings``: exact and fast oracle on the tiny scan, direct
+back-projection on the tiny scan in full and on a voxel sample of the
+realistic scan) and, unless ``--no-extras``, compact records of the other
+workloads: ``batch`` (the 64-scan uneven mix), ``serve`` (Poisson stream,
+FP16-stored served form against the plain FP32 form) and ``large_storage``
+(the large scan with FP32, FP16 and BF16 echo storage against the oracle).
 """
 from __future__ import annotations
 
@@ -54,6 +60,11 @@ def parse_args():
     ap.add_argument("--mix", type=int, default=64, help="scans in the batched mix")
     ap.add_argument("--requests", type=int, default=256, help="requests in the serving run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-traffic", default=None, metavar="CSV",
+                    help="write profiles/ncu_traffic.json from an ncu launch list (CSV) and exit")
+    ap.add_argument("--ncu-command", default="", help="the command that produced --ncu-traffic's CSV")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch / serve / large_storage records of the default run")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default gridding launch shape")
     ap.add_argument("--tiles", default=None,
@@ -122,6 +133,17 @@ def make_scan(workload: str, rank: int):
     return synth.realistic(seed=2000 + rank)
 
 
+def plan_geometry(scan, nufft_tol=1e-3):
+    """Kernel width and spectral grid the library's plan picks for a scan
+    with default options (the same rules, restated for reporting only: the
+    smallest Gaussian width whose gridding error is within the tolerance,
+    and the next power of two >= the voxel count per axis, at least 16)."""
+    errs = {4: 4.8e-3, 5: 1.4e-3, 6: 5.5e-4, 7: 1.5e-4, 8: 5.4e-5, 9: 1.6e-5, 10: 4.4e-6, 11: 1.3e-6, 12: 3.5e-7}
+    w = next((k for k in sorted(errs) if errs[k] <= nufft_tol), 12)
+    p2 = lambda n: max(16, 1 << max(0, (n - 1).bit_length()))
+    return {"kernel_width": w, "spectral_grid": [p2(scan.grid.nx), p2(scan.grid.ny)], "nufft_tol": nufft_tol}
+
+
 def workload_config(scan, workload, plan=None):
     T, R, P, Nk = scan.echo.shape
     g = scan.grid
@@ -137,7 +159,36 @@ def workload_config(scan, workload, plan=None):
     if plan is not None:
         cfg.update({"kernel_width": plan.kernel_width, "spectral_grid": [plan.mx, plan.my],
                     "nufft_tol": plan.opt.nufft_tol})
+    else:
+        cfg.update(plan_geometry(scan))
     return cfg
+
+
+def host_cpu():
+    """(model name, logical cores) of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return model or platform.processor() or platform.machine(), os.cpu_count() or 1
+
+
+def oracle_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -269,6 +320,86 @@ def csrc_digest(files=None):
     for p in files:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
+
+
+# kernels of one image in launch order, by stage (name fragments of the kernels)
+STAGE_SOURCES = {
+    "compensate": ["paper_2305_02064_gb300/csrc/samples.cu"],
+    "grid": ["paper_2305_02064_gb300/csrc/spread.cu", "paper_2305_02064_gb300/csrc/grid_tc.cu"],
+    "fft_x": ["paper_2305_02064_gb300/csrc/fft_kernels.cu"],
+    "fft_y": ["paper_2305_02064_gb300/csrc/fft_kernels.cu"],
+    "stolt": ["paper_2305_02064_gb300/csrc/stolt.cu"],
+    "ifft_y": ["paper_2305_02064_gb300/csrc/fft_kernels.cu"],
+    "ifft_x": ["paper_2305_02064_gb300/csrc/fft_kernels.cu"],
+}
+COMMON_SOURCES = ["paper_2305_02064_gb300/csrc/fft.cuh", "paper_2305_02064_gb300/csrc/internal.cuh",
+                  "include/mmsar.h"]
+
+
+def stage_of_kernel(name: str, fft_seen: int):
+    """Stage of a kernel of the imaging sequence (None for prep kernels);
+    the column FFT kernel serves four stages, told apart by launch order."""
+    if "compensate" in name:
+        return "compensate"
+    if "spread" in name or "grid_tc" in name:
+        return "grid"
+    if "stolt" in name:
+        return "stolt"
+    if "column_fft" in name:
+        return ("fft_x", "fft_y", "ifft_y", "ifft_x")[fft_seen % 4]
+    return None
+
+
+def write_ncu_traffic(csv_path: str, command: str, workload: str = "realistic"):
+    """profiles/ncu_traffic.json from an ncu launch list taken with
+    --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+    --csv: per stage the DRAM bytes (read + write) and time of its kernel in
+    the last complete image of the list, with the digest of the sources that
+    kernel is built from (so the bench uses it only while they are unchanged)."""
+    import csv
+    launches = {}
+    order = []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        lid = row["ID"]
+        if lid not in launches:
+            launches[lid] = {"kernel": row["Kernel Name"], "m": {}}
+            order.append(lid)
+        v = row["Metric Value"].replace(",", "")
+        unit = row.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-3, "usecond": 1.0,
+                 "msecond": 1e3}.get(unit, 1)
+        launches[lid]["m"][row["Metric Name"]] = float(v) * scale
+    # the last image: from the last prep launch (zref) on
+    starts = [i for i, lid in enumerate(order) if "zref" in launches[lid]["kernel"]]
+    stages = {}
+    for st in starts[::-1]:
+        seq, fft_seen = {}, 0
+        for lid in order[st:]:
+            k = launches[lid]["kernel"]
+            stage = stage_of_kernel(k, fft_seen)
+            if "column_fft" in k:
+                fft_seen += 1
+            if stage and stage not in seq:
+                seq[stage] = launches[lid]
+        if len(seq) == len(STAGE_SOURCES):
+            stages = seq
+            break
+    out = {"workload": workload, "command": command,
+           "note": "dram__bytes_read.sum + dram__bytes_write.sum of each kernel in the last complete image of the "
+                   "launch list; sha = digest of the listed sources the kernel is built from",
+           "stages": {}}
+    for stage, l in stages.items():
+        srcs = [p for p in STAGE_SOURCES[stage] if os.path.exists(os.path.join(ROOT, p))] + COMMON_SOURCES
+        m = l["m"]
+        out["stages"][stage] = {"kernel": l["kernel"][:60], "sources": srcs, "sha": csrc_digest(srcs),
+                                "dram_bytes_per_launch": m.get("dram__bytes_read.sum", 0) +
+                                m.get("dram__bytes_write.sum", 0),
+                                "us": m.get("gpu__time_duration.sum", 0)}
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    return out
 
 
 def ncu_traffic(stage: str, workload: str):
@@ -458,8 +589,9 @@ def cpu_baseline(scan, vol_gpu, compensate=1):
     ref = rma.rma_fast(su)
     dt = time.time() - t0
     got = vol_gpu.cpu().numpy()
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return ({"value": scan.grid.n_voxels / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    cores = oracle_cores()
+    return ({"value": scan.grid.n_voxels / dt, "unit": UNIT, "cores": cores, "cpu_model": host_cpu()[0],
+             "kind": "oracle",
              "sample": "one whole scan of the workload through oracle.rma.rma_fast (FP64 Gaussian gridding w=16, "
                        "OpenMP + scipy.fft workers on all cores)", "seconds": dt},
             {"nmse_vs_oracle": float(rma.nmse(got, ref)), "peak_match": rma.peak_index(got) == rma.peak_index(ref)})
@@ -508,6 +640,76 @@ def storage_comparison(scan, vol_fp32, args):
     return out
 
 
+def oracle_timings(scan_realistic, n_sample_voxels=16):
+    """The oracles timed on the host cores (OpenMP on every core): on the
+    tiny scan the exact oracle, the fast oracle and the direct
+    back-projection over its whole volume; on the realistic scan the direct
+    back-projection at a voxel sample (the voxels of its first scatterers
+    plus seeded random voxels), reported per voxel with the full-volume time
+    extrapolated from it (labelled as such)."""
+    import numpy as np
+    import synth
+    from oracle import bpa, rma
+    out = {"cores": oracle_cores(), "cpu_model": host_cpu()[0]}
+    tiny = synth.tiny()
+    su = rma.setup_from(tiny)
+    for name, fn in (("rma_exact_tiny_s", lambda: rma.rma_exact(su)), ("rma_fast_tiny_s", lambda: rma.rma_fast(su)),
+                     ("bpa_tiny_full_s", lambda: bpa.bpa(tiny))):
+        t0 = time.time()
+        fn()
+        out[name] = time.time() - t0
+    g = scan_realistic.grid
+    rng = np.random.default_rng(17)
+    half = n_sample_voxels // 2
+    near = []
+    for x, y, z, _ in scan_realistic.scatterers[:half]:
+        i, j, q = g.centre_index(x, y, z)
+        near.append((i * g.ny + j) * g.nz + q)
+    idx = np.unique(np.concatenate([np.asarray(near, np.int64),
+                                    rng.integers(0, g.n_voxels, n_sample_voxels - len(near))]))
+    t0 = time.time()
+    bpa.bpa(scan_realistic, idx)
+    dt = time.time() - t0
+    out["bpa_realistic_sample"] = {"voxels": int(idx.size), "seconds": dt, "s_per_voxel": dt / idx.size,
+                                   "full_volume_s_extrapolated": dt / idx.size * g.n_voxels,
+                                   "note": "extrapolated linearly from the sample to all 256x256x64 voxels"}
+    return out
+
+
+def run_large_storage(args, dist):
+    """The large scan (3 Tx x 4 Rx, 256 x 256 positions, Nk = 512 ->
+    512 x 512 x 128 voxels) imaged with FP32, FP16 and BF16 echo storage;
+    device ms per image and NMSE against the FP64 oracle for each."""
+    import numpy as np
+    import torch
+    import paper_2305_02064_gb300 as mm
+    dev = torch.device(f"cuda:{dist.local_rank}")
+    scan = make_scan("large", dist.rank)
+    plan = mm.Plan.for_scan(scan, compensate=args.compensate)
+    echo = torch.from_numpy(np.ascontiguousarray(scan.echo)).to(dev)
+    pos, tx, rx = (torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev) for a in (scan.pos, scan.tx, scan.rx))
+    ws, vol = plan.new_workspace(dev), plan.new_volume(dev)
+    for _ in range(3):
+        plan.image(ws, echo, pos, tx, rx, vol)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, args.steps // 10)
+    e0.record()
+    for _ in range(n):
+        plan.image(ws, echo, pos, tx, rx, vol)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    plan.poll_error(ws)
+    fp32_ms = e0.elapsed_time(e1) / n
+    del ws, echo
+    out = storage_comparison(scan, vol, args)
+    out.setdefault("fp32", {})["ms_per_image"] = fp32_ms
+    out["fp32"]["voxels_per_s"] = scan.grid.n_voxels / (fp32_ms * 1e-3)
+    out["workload"] = workload_config(scan, "large", plan)["workload"]
+    out["oracle"] = "oracle.rma.rma_fast, FP64 Gaussian gridding w=12 (relative error ~1e-6 per transform)"
+    return out
+
+
 # ----------------------------------------------------------------------------- reference (oracle) arm
 def run_reference(args, dist):
     from oracle import rma
@@ -515,25 +717,21 @@ def run_reference(args, dist):
         return None
     scan = make_scan(args.workload, 0)
     su = rma.setup_from(scan, compensate=args.compensate)
-    nk = su.n_k
-    ks = max(1, nk // 8)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.time()
-        rma.rma_fast(su, k_slice=slice(0, ks))
+        rma.rma_fast(su)
         if i >= args.warmup:
             times.append(time.time() - t0)
-    vox_eq = scan.grid.n_voxels * ks / nk
     sec = statistics.mean(times)
-    value = vox_eq / sec
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = (f"first {ks} of {nk} frequencies of the scan through oracle.rma.rma_fast (FP64, w=16); "
-              f"the image is linear in the frequency samples, so voxels/s = voxels * {ks}/{nk} / step time")
+    value = scan.grid.n_voxels / sec
+    sample = "one whole image of the scan per step through oracle.rma.rma_fast (FP64 Gaussian gridding, w=16)"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(scan, args.workload),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores(), "cpu_model": host_cpu()[0],
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -759,8 +957,43 @@ def run_psf(args, dist):
             "ms_per_image_mean": round(float(np.mean(t_img)), 4), "rows": rows}
 
 
+def extras(args, dist):
+    """Compact records of the batched, served and large workloads for the
+    default run (each a few tens of seconds, inputs generated on the host)."""
+    import torch
+    out = {}
+    t0 = time.time()
+    b = run_batch(args, dist)
+    out["batch"] = {"images_per_s": b["value"], "ms_per_mix": b["ms_per_step"], "scans": args.mix,
+                    "form": b["config"]["workload"], "launches_per_mix": b["modes_launches_per_mix"],
+                    "modes_ms_per_mix": b["modes_ms_per_mix"], "voxels_per_s": b["voxels_per_s"],
+                    "dtype": b["dtype"], "wall_s": time.time() - t0}
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    sv = run_serve(args, dist)
+    f = sv["forms"]
+    out["serve"] = {k: {"p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"], "images_per_s": v["images_per_s"],
+                        "saturated_images_per_s": v["saturated"]["images_per_s"],
+                        "max_concurrent": v["max_concurrent"]} for k, v in f.items()}
+    out["serve"].update({"arrivals": "Poisson 200 req/s", "requests": args.requests,
+                         "worst_nmse_served_vs_plain_fp32": sv["worst_nmse_served_vs_plain_fp32"],
+                         "wall_s": time.time() - t0})
+    for k in ("peak_admitted_gb", "peak_device_gb", "cap_gb"):
+        if k in f.get("served_f16", {}):
+            out["serve"][k] = f["served_f16"][k]
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    out["large_storage"] = run_large_storage(args, dist)
+    out["large_storage"]["wall_s"] = time.time() - t0
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse_args()
+    if args.ncu_traffic:
+        print(json.dumps(write_ncu_traffic(args.ncu_traffic, args.ncu_command, args.workload), indent=1))
+        return 0
     if args.impl == "reference":
         dist = Dist(want_cuda=False)
         out = run_reference(args, dist)
@@ -788,6 +1021,14 @@ def main():
         cb, acc = cpu_baseline(scan, vol, args.compensate)
         res["cpu_baseline"] = cb
         res["accuracy"] = acc
+        if args.workload == "realistic":
+            res["oracle_timings"] = oracle_timings(scan)
+            res["oracle_timings"]["rma_fast_realistic_s"] = cb["seconds"]
+    if dist.world == 1 and args.workload == "realistic" and not args.no_extras:
+        import torch
+        del vol
+        torch.cuda.empty_cache()
+        res.update(extras(args, dist))
     if dist.rank == 0:
         print(json.dumps(res))
     dist.close()

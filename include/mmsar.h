@@ -33,8 +33,12 @@
  * - Output voxel (i, j, q) has centre (x0 + i dx, y0 + j dy, z0 + q dz) and
  *   is stored at vol[(i * ny + j) * nz + q] (z fastest), complex64.
  * - The image is normalised by 1 / (n_tx n_rx n_pos n_k).
- * - No C++ exception crosses this boundary.  A plan is not thread-safe; use
- *   one plan (and one workspace) per concurrently running stream.
+ * - No C++ exception crosses this boundary.  The imaging calls only read
+ *   the plan, so one plan may serve several streams or threads at once as
+ *   long as every call in flight has its own workspace.  The calls that
+ *   change a plan (mmsar_plan_set_tiles, mmsar_plan_set_stage_events,
+ *   mmsar_plan_destroy) must not run while another thread uses that plan;
+ *   stage events set on a plan are recorded by every call that uses it.
  */
 #ifndef MMSAR_H
 #define MMSAR_H
@@ -135,7 +139,8 @@ typedef struct {
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the
  * Python package times the shapes on the caller's data and sets the
- * fastest.  INVALID_ARG for other values.  Not thread-safe (like the plan). */
+ * fastest.  INVALID_ARG for other values.  Changes the plan: not while another
+ * thread images with it. */
 mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles);
 mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles);
 
@@ -215,7 +220,9 @@ mmsar_status mmsar_image_batch_fused(const mmsar_request *reqs, int n, void *str
 
 /* Read (and clear) the device error word of the last call that used this
  * workspace: synchronises `stream`, returns MMSAR_OK or the first device-side
- * condition (MMSAR_ERR_NONFINITE, MMSAR_ERR_INVALID_ARG for Z_c <= 0). */
+ * condition (MMSAR_ERR_NONFINITE, MMSAR_ERR_INVALID_ARG for Z_c <= 0).
+ * workspace == NULL reads the built-in scratch area of mmsar_image_static on
+ * the current device (the error word of the last static call there). */
 mmsar_status mmsar_poll_error(const void *workspace, void *stream);
 
 /* Peak voxel of a complex64 volume (utility; Sec. V compares images by
@@ -235,10 +242,16 @@ mmsar_status mmsar_peak(const void *vol, int64_t n, void *scratch, void *result,
  * mmsar_static_workspace_bytes() bytes (32 MiB) that every GPU using the
  * library holds until the process exits.  Arguments as for mmsar_image; the
  * caller still passes inputs and the output.  Plans whose workspace exceeds
- * the area are rejected with MMSAR_ERR_UNSUPPORTED_SIZE.  The first call on
- * each device looks up the area's device address (make it before any stream
- * capture).  All calls on a device share the area: calls that overlap on the
- * GPU race on it, so serialise them.  No device memory is allocated. */
+ * the area are rejected with MMSAR_ERR_UNSUPPORTED_SIZE.  A call made outside
+ * stream capture looks up the area's device address on the current device
+ * (so a device reset, which may move it, is followed correctly) and keeps
+ * it; a call made while `stream` is being captured uses the address kept by
+ * the last plain call on that device and fails with MMSAR_ERR_INVALID_ARG if
+ * there was none, so make one plain call on each device before any stream
+ * capture (and again after a device reset).  All calls on a device share the
+ * area: calls that overlap on the GPU race on it, so serialise them.  The
+ * device error word of the last call is read with
+ * mmsar_poll_error(NULL, stream).  No device memory is allocated. */
 size_t mmsar_static_workspace_bytes(void);
 mmsar_status mmsar_image_static(mmsar_plan *plan, const void *echo, const float *echo_scale,
                                 const double *pos, const double *tx, const double *rx,

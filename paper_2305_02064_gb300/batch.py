@@ -12,23 +12,38 @@ library's; this module only marshals pointers and streams.
 """
 from __future__ import annotations
 
+import collections
 import ctypes
+import threading
 
 from . import Plan, _lib, _ptr, quantize_echo
 
-_PLAN_CACHE: dict = {}
+# Plans are host-only and reusable: the imaging calls only read a plan, so
+# one plan serves every scan of its shape on any stream (each call with its
+# own workspace).  The cache keeps the most recently used PLAN_CACHE_MAX
+# plans; an evicted plan lives on while a job still holds it.
+PLAN_CACHE_MAX = 256
+_PLAN_CACHE: "collections.OrderedDict" = collections.OrderedDict()
+_PLAN_LOCK = threading.Lock()
 
 
 def plan_for(scan, dtype="c64", **kw):
-    """A plan per (shape, grid, dtype, options); plans are host-only and reusable."""
+    """A plan per (shape, grid, dtype, options), from a bounded LRU cache."""
     T, R, P, Nk = scan.echo.shape
     g = scan.grid
     key = (T, R, P, Nk, scan.f0, scan.df, g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, g.nx, g.ny, g.nz, dtype,
            tuple(sorted(kw.items())))
-    p = _PLAN_CACHE.get(key)
-    if p is None:
-        p = Plan.for_scan(scan, dtype=dtype, **kw)
-        _PLAN_CACHE[key] = p
+    with _PLAN_LOCK:
+        p = _PLAN_CACHE.get(key)
+        if p is not None:
+            _PLAN_CACHE.move_to_end(key)
+            return p
+    p = Plan.for_scan(scan, dtype=dtype, **kw)
+    with _PLAN_LOCK:
+        p = _PLAN_CACHE.setdefault(key, p)
+        _PLAN_CACHE.move_to_end(key)
+        while len(_PLAN_CACHE) > PLAN_CACHE_MAX:
+            _PLAN_CACHE.popitem(last=False)
     return p
 
 

@@ -228,6 +228,10 @@ cudaError_t launch_stolt_multi(const mmsar_request *r, int n, cudaStream_t s);
 // Record a formatted message for mmsar_last_error() and return `st`.
 mmsar_status report_error(mmsar_status st, const char *fmt, ...);
 
+// Device address of the built-in scratch area of mmsar_image_static on the
+// current device (looked up afresh unless `s` is being captured).
+mmsar_status static_workspace_address(cudaStream_t s, void **out);
+
 // Raise a kernel's dynamic shared-memory limit once per device (the
 // attribute is per device; the first launch on each device sets it).
 cudaError_t ensure_smem_attr(const void *func, size_t bytes);

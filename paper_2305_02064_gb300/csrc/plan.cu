@@ -446,8 +446,13 @@ mmsar_status mmsar_image_batch_fused(const mmsar_request *reqs, int n, void *str
 }
 
 mmsar_status mmsar_poll_error(const void *workspace, void *stream) {
-    if (!workspace) return fail(MMSAR_ERR_INVALID_ARG, "null workspace");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!workspace) {   // the built-in scratch area of mmsar_image_static on the current device
+        void *ws = nullptr;
+        const mmsar_status st = static_workspace_address(s, &ws);
+        if (st != MMSAR_OK) return st;
+        workspace = ws;
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "synchronising the stream");
     int word = 0;

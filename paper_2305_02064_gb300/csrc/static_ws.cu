@@ -12,14 +12,20 @@
 // file-scope __device__ array of kStaticWsBytes.  Every GPU on which the
 // library is used holds that array from module load until the process exits.
 //
-// The first call on each device looks up the array's device address with
-// cudaGetSymbolAddress while that device is current and keeps it; make that
-// first call on each device before any stream capture begins.  All calls on
-// a device share the one array: calls whose work overlaps on the GPU (two
-// streams, or two threads) race on it and must be serialised by the caller.
-// The array keeps the previous call's contents; mmsar_image clears the parts
-// that must start at zero (error word, bin counters) at the start of every
-// call and overwrites everything else it reads.
+// In host code the array's name is only a host-side stand-in, so the device
+// address is looked up with cudaGetSymbolAddress while the device is
+// current.  A call made outside stream capture looks it up afresh (a device
+// reset reloads the module, and the array may then sit elsewhere) and
+// remembers it for its device; a call made while its stream is being
+// captured cannot do that lookup and uses the address remembered by the last
+// plain call on the device, so make one plain call on each device before any
+// stream capture (and again after a device reset).  All calls on a device
+// share the one array: calls whose work overlaps on the GPU (two streams, or
+// two threads) race on it and must be serialised by the caller.  The array
+// keeps the previous call's contents; mmsar_image clears the parts that must
+// start at zero (error word, bin counters) at the start of every call and
+// overwrites everything else it reads.  The error word sits at the start of
+// the array: mmsar_poll_error(NULL, stream) reads it.
 #include <mutex>
 
 #include "internal.cuh"
@@ -36,6 +42,35 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 }  // namespace
 
+mmsar_status static_workspace_address(cudaStream_t s, void **out) {
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return report_error(MMSAR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return report_error(MMSAR_ERR_UNSUPPORTED_SIZE, "device %d beyond the %d supported", dev, kMaxDevices);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();   // not sticky; treat the stream as capturing
+        cs = cudaStreamCaptureStatusActive;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (cs == cudaStreamCaptureStatusNone) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e != cudaSuccess || !p)
+            return report_error(MMSAR_ERR_CUDA, "looking up the static scratch area: %s", cudaGetErrorString(e));
+        g_addr[dev] = p;
+    } else if (!g_addr[dev]) {
+        return report_error(MMSAR_ERR_INVALID_ARG,
+                            "mmsar_image_static under stream capture needs one plain call on device %d first "
+                            "(to look up its scratch area)", dev);
+    }
+    *out = g_addr[dev];
+    return MMSAR_OK;
+}
+
 }  // namespace mmsar
 
 using namespace mmsar;
@@ -51,22 +86,8 @@ extern "C" mmsar_status mmsar_image_static(mmsar_plan *plan, const void *echo, c
                             "this scan needs %zu bytes of scratch; the built-in scratch area of "
                             "mmsar_image_static holds %zu bytes (use mmsar_image with a workspace)",
                             plan->p.ws_bytes, kStaticWsBytes);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return report_error(MMSAR_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices)
-        return report_error(MMSAR_ERR_UNSUPPORTED_SIZE, "device %d beyond the %d supported", dev, kMaxDevices);
     void *ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_static_workspace);
-            if (e != cudaSuccess || !p)
-                return report_error(MMSAR_ERR_CUDA, "looking up the static scratch area: %s", cudaGetErrorString(e));
-            g_addr[dev] = p;
-        }
-        ws = g_addr[dev];
-    }
+    const mmsar_status st = static_workspace_address(reinterpret_cast<cudaStream_t>(stream), &ws);
+    if (st != MMSAR_OK) return st;
     return mmsar_image(plan, ws, kStaticWsBytes, echo, echo_scale, pos, tx, rx, vol, stream);
 }

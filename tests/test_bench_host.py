@@ -62,3 +62,61 @@ def test_stage_bytes_add_up():
     V = scan.grid.nx * scan.grid.ny * scan.grid.nz * 8
     assert nb["ifft_x"] >= V and nb["stolt"] >= plan.mx * plan.my * scan.grid.nz * 8
     assert set(nb) >= {"prep", "compensate", "grid", "fft_x", "fft_y", "stolt", "ifft_y", "ifft_x"}
+
+
+def _ncu_rows(kernels):
+    """An ncu --csv launch list: per launch, duration and DRAM bytes."""
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",' \
+          '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    out = ["==PROF== Connected to process 1\n", hdr]
+    for i, (k, us, rd, wr) in enumerate(kernels):
+        for name, unit, v in (("dram__bytes_read.sum", "Mbyte", rd), ("dram__bytes_write.sum", "Mbyte", wr),
+                              ("gpu__time_duration.sum", "usecond", us)):
+            out.append(f'"{i}","1","python","h","{k}","1","7","(256, 1, 1)","(1, 1, 1)","0","10.3",'
+                       f'"Command line profiler metrics","{name}","{unit}","{v}"\n')
+    return "".join(out)
+
+
+def test_ncu_traffic_writer_takes_the_last_complete_image(tmp_path, monkeypatch):
+    image = [("zref_kernel(ZrefArgs)", 10, 0.1, 0.1), ("geometry_kernel(GeomArgs)", 30, 0.2, 0.2),
+             ("bin_scatter_kernel(ScatterArgs)", 5, 0.1, 0.1), ("void compensate_kernel<0, 1>(A)", 90, 300, 225),
+             ("void spread_kernel<2, 4, 8, 4>(SpreadArgs)", 290, 310, 134),
+             ("void column_fft_reg_kernel<512, -1, 1>(ColumnFFT)", 80, 130, 110),
+             ("void column_fft_reg_kernel<512, -1, 1>(ColumnFFT)", 67, 110, 115),
+             ("void stolt_kernel<128, 8, 17, 2>(StoltArgs)", 92, 100, 28),
+             ("void column_fft_reg_kernel<256, 1, 1>(ColumnFFT)", 17, 17, 17),
+             ("void column_fft_reg_kernel<256, 1, 1>(ColumnFFT)", 16, 16, 17.5)]
+    second = [(k, us, rd * 2, wr) for (k, us, rd, wr) in image]
+    csv_path = tmp_path / "launches.csv"
+    csv_path.write_text(_ncu_rows(image + second + image[:4]))   # the last image is incomplete
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    for p in set(sum(bench.STAGE_SOURCES.values(), [])) | set(bench.COMMON_SOURCES):
+        (tmp_path / p).parent.mkdir(parents=True, exist_ok=True)
+        (tmp_path / p).write_text("// " + p)
+    d = bench.write_ncu_traffic(str(csv_path), "ncu ... python bench.py")
+    assert set(d["stages"]) == set(bench.STAGE_SOURCES)
+    assert d["stages"]["grid"]["dram_bytes_per_launch"] == (620 + 134) * 1e6     # from the second image
+    assert d["stages"]["ifft_x"]["dram_bytes_per_launch"] == (32 + 17.5) * 1e6
+    assert d["stages"]["fft_y"]["us"] == 67
+    assert bench.ncu_traffic("grid", "realistic") == (620 + 134) * 1e6
+
+
+def test_plan_geometry_matches_the_library_plan():
+    """The reference arm reports the plan's kernel width and spectral grid
+    without loading the library; the rule it restates agrees with the plan."""
+    import synth
+    from paper_2305_02064_gb300 import Plan
+    for kw in ({"nx": 24, "ny": 12, "nz": 10}, {"nx": 64, "ny": 100, "nz": 8}, {"nx": 8, "ny": 8, "nz": 4}):
+        scan = synth.custom(nx_pos=4, ny_pos=4, nk=8, **kw)
+        for tol in (1e-3, 1e-4, 1e-6):
+            g = bench.plan_geometry(scan, tol)
+            plan = Plan.for_scan(scan, nufft_tol=tol)
+            assert g["kernel_width"] == plan.kernel_width
+            assert g["spectral_grid"] == [plan.mx, plan.my]
+
+
+def test_host_cpu_reports_a_model():
+    model, cores = bench.host_cpu()
+    assert isinstance(model, str) and model
+    assert cores >= 1

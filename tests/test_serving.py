@@ -90,3 +90,20 @@ def test_latency_summary_and_arrivals():
     t = poisson_arrivals(2000, rate_hz=200.0, seed=1)
     assert (t[1:] > t[:-1]).all()
     assert 1 / 200 * 0.9 < (t[-1] / len(t)) < 1 / 200 * 1.1
+
+
+def test_plan_cache_is_bounded_and_shares_plans(monkeypatch):
+    """One plan per scan shape (plans are only read by the imaging calls),
+    the least recently used evicted beyond the cache size."""
+    import synth
+    from paper_2305_02064_gb300 import batch
+    monkeypatch.setattr(batch, "PLAN_CACHE_MAX", 3)
+    batch._PLAN_CACHE.clear()
+    scans = [synth.custom(nx_pos=2, ny_pos=2, nk=8, nx=8 + 8 * i, ny=8, nz=4) for i in range(5)]
+    p0 = batch.plan_for(scans[0])
+    assert batch.plan_for(scans[0]) is p0
+    for s in scans[1:]:
+        batch.plan_for(s)
+    assert len(batch._PLAN_CACHE) == 3
+    assert batch.plan_for(scans[0]) is not p0        # evicted, rebuilt
+    batch._PLAN_CACHE.clear()
