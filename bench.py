@@ -68,7 +68,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default gridding launch shape")
     ap.add_argument("--tiles", default=None,
-                    help="gridding launch shape 'nf,warps,grouped' instead of the autotuner's (single-scan workloads)")
+                    help="gridding form 'nf,warps,grouped[,tensor_cores]' instead of the autotuner's "
+                         "(single-scan workloads; '2,4,0,v' = tensor cores, pipeline v = 1..4)")
     return ap.parse_args()
 
 
@@ -293,7 +294,13 @@ def stage_bytes(plan, scan):
     Z = mx * my * nz * c
     B = mx * ny * nz * c
     V = nx * ny * nz * c
-    rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 8   # weight record + (in-bin offset, sample index)
+    if plan.tiles[3]:
+        # tensor-core form: s_hat as FP16 hi / lo planes (the same bytes as
+        # complex64), a 16-byte record per sample (bin order) and one
+        # normalisation exponent byte per sample and 64-frequency group
+        rec = 16 + nkp // 64 + (1 if nkp % 64 else 0)
+    else:
+        rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 8   # weight record + (in-bin offset, sample index)
     # prep: geometry records, phases, bin ids, permutation; compensate: echo
     # in, s_hat out, phases, and (same launch) the in-bin sort and records
     return {"prep": L * 36 + 24 * P, "compensate": echo + shat + L * 8 + L * (24 + rec), "grid": shat + G + L * rec,
@@ -571,10 +578,11 @@ def run_ours(args, dist):
                 "serial_ms_per_step": e2e_serial_ms, "serial_value": total_vox / (e2e_serial_ms * 1e-3)},
         "gpu_launches": plan.kernels_per_image * args.steps,
         "clocks": clk,
-        "grid_launch_shape": {"freqs_per_lane": plan.tiles[0], "warps_per_cta": plan.tiles[1],
-                              "grouped": plan.tiles[2],
+        "grid_launch_shape": {"tensor_cores": plan.tiles[3], "freqs_per_lane": plan.tiles[0],
+                              "warps_per_cta": plan.tiles[1], "grouped": plan.tiles[2],
                               "autotuned_ms": None if tuned is None else
-                              {f"{a}x{b}{'g' if c else ''}": round(v, 4) for (a, b, c), v in tuned["ms"].items()}},
+                              {(f"tc{t}" if t else f"{a}x{b}{'g' if c else ''}"): round(v, 4)
+                               for (a, b, c, t), v in tuned["ms"].items()}},
     }
     return res, scan, vol
 
@@ -806,7 +814,8 @@ def run_batch(args, dist):
     best = ms[best_mode]
     shapes = {}
     for t in tuned:
-        key = f"{t['tiles'][0]} freq/lane, {t['tiles'][1]} warps" + (", grouped" if t['tiles'][2] else "")
+        key = (f"tensor cores {t['tiles'][3]}" if t['tiles'][3] else
+               f"{t['tiles'][0]} freq/lane, {t['tiles'][1]} warps" + (", grouped" if t['tiles'][2] else ""))
         shapes[key] = shapes.get(key, 0) + 1
     n_img = len(jobs) * dist.world
     forms = {"graph": "one CUDA graph of the mix on 4 streams, ten launches per scan",
@@ -851,9 +860,11 @@ def run_serve(args, dist):
     arrivals = poisson_arrivals(args.requests, 200.0, seed=11 + dist.rank)
     out = {}
     results = {}
+    cap = 40 << 30
     for name, dtype, slots in (("served_f16", "f16", 8), ("plain_fp32", "c64", 1)):
-        ex = GpuExecutor(dev, dtype=dtype, n_streams=slots)
-        ex.reserve(pool)   # every slot's device buffers sized for the largest scan of the mix
+        # one device arena of the admission cap, allocated before serving:
+        # every admitted request's buffers are placed in it
+        ex = GpuExecutor(dev, dtype=dtype, n_streams=slots, mem_cap=cap)
         # page-locked inputs once per distinct scan, shared by its requests
         pinned = []
         for sc in pool:
@@ -864,26 +875,33 @@ def run_serve(args, dist):
                              pinned=pinned[picks[i]]) for i in range(args.requests)]
         # one untimed pass over the same stream warms plans, kernel attributes,
         # the device allocator and the pinned output pool
-        Scheduler(ex, slots=slots, mem_cap=40 << 30).run(
+        Scheduler(ex, slots=slots, mem_cap=cap).run(
             [ServeRequest(r.rid, r.scan, r.arrival, r.footprint, pinned=r.pinned) for r in reqs])
         torch.cuda.synchronize(dev)
         dist.barrier()
-        sch = Scheduler(ex, slots=slots, mem_cap=40 << 30)
+        alloc0 = torch.cuda.memory_allocated(dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        ex.arena.peak = ex.arena.in_use
+        sch = Scheduler(ex, slots=slots, mem_cap=cap)
         done = sch.run(reqs)
         out[name] = latency_summary(done)
         out[name]["max_concurrent"] = sch.max_concurrent
-        out[name]["peak_admitted_gb"] = sch.peak_in_use / 2 ** 30
+        out[name]["peak_admitted_gb"] = ex.arena.peak / 2 ** 30
+        out[name]["cap_gb"] = cap / 2 ** 30
+        out[name]["allocated_while_serving_bytes"] = int(torch.cuda.max_memory_allocated(dev) - alloc0)
         # capacity: the same requests all arriving at once (after one untimed
         # burst that grows the pinned output pool to the slot count)
         burst = lambda: [ServeRequest(r.rid, r.scan, 0.0, r.footprint, pinned=r.pinned) for r in reqs]
-        Scheduler(ex, slots=slots, mem_cap=40 << 30).run(burst())
+        Scheduler(ex, slots=slots, mem_cap=cap).run(burst())
         torch.cuda.synchronize(dev)
-        out[name]["saturated"] = latency_summary(Scheduler(ex, slots=slots, mem_cap=40 << 30).run(burst()))
+        out[name]["saturated"] = latency_summary(Scheduler(ex, slots=slots, mem_cap=cap).run(burst()))
         # volumes for the accuracy comparison, outside the timed run
         ex.keep = True
         check = [ServeRequest(i, pool[i], 0.0, ex.footprint(pool[i]), pinned=pinned[i]) for i in range(len(pool))]
-        Scheduler(ex, slots=slots, mem_cap=40 << 30).run(check)
+        Scheduler(ex, slots=slots, mem_cap=cap).run(check)
         results[name] = {r.rid: r.result for r in check}
+        del ex
+        torch.cuda.empty_cache()
     # accuracy of the served form against the plain FP32 form, per scan of the pool
     worst = float(max(rma.nmse(results["served_f16"][i].numpy(), results["plain_fp32"][i].numpy())
                       for i in range(len(pool))))
@@ -893,7 +911,8 @@ def run_serve(args, dist):
             "steps": args.requests, "warmup": len(pool), "ms_per_step": 1e3 / s["images_per_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "fp16 storage, fp32 arithmetic", "data": "synthetic (seeded batched mix)",
-            "config": {"workload": "serving: Poisson 200 req/s, continuous batching (8 slots), 40 GB admission cap",
+            "config": {"workload": "serving: Poisson 200 req/s, continuous batching (8 slots), requests placed in "
+                                   "one 40 GiB device arena",
                        "requests": args.requests},
             "latency_ms": {"p50": s["p50_ms"], "p99": s["p99_ms"]},
             "forms": out, "worst_nmse_served_vs_plain_fp32": worst}
@@ -978,9 +997,8 @@ def extras(args, dist):
     out["serve"].update({"arrivals": "Poisson 200 req/s", "requests": args.requests,
                          "worst_nmse_served_vs_plain_fp32": sv["worst_nmse_served_vs_plain_fp32"],
                          "wall_s": time.time() - t0})
-    for k in ("peak_admitted_gb", "peak_device_gb", "cap_gb"):
-        if k in f.get("served_f16", {}):
-            out["serve"][k] = f["served_f16"][k]
+    for k in ("peak_admitted_gb", "cap_gb", "allocated_while_serving_bytes"):
+        out["serve"][k] = {n: f[n].get(k) for n in f}
     torch.cuda.empty_cache()
     t0 = time.time()
     out["large_storage"] = run_large_storage(args, dist)

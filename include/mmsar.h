@@ -123,7 +123,8 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
  * the per-sample shapes, to rounding between the per-sample and the grouped
  * form (another summation order); they differ in speed, which depends on the
  * scan (small scans fill the GPU better with smaller CTAs; arrays whose Tx
- * and Rx lie on one line along y give large groups).  Defaults: 2, 4, 0. */
+ * and Rx lie on one line along y give large groups).  The tensor-core form
+ * agrees with them to FP32 rounding.  Defaults: 2, 4, 0, 0. */
 typedef struct {
     int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64; 4: 128,   *
                                 * in 4 x 2-cell warp blocks (fewer taps outside   *
@@ -135,6 +136,17 @@ typedef struct {
                                 * gridded together, the x weights applied once to *
                                 * their y-weighted sum (needs n_tx n_rx <= 16);   *
                                 * 0: sample by sample                              */
+    int grid_tensor_cores;     /* 1 .. 4: the gridding runs on the tensor cores as *
+                                * a per-tile product weights x samples, FP32-     *
+                                * accurate (FP16 hi/lo operands, FP32             *
+                                * accumulation); the value picks the pipeline     *
+                                * (samples per MMA chunk / stages / chunks        *
+                                * gathered ahead / list capacity / CTAs per SM:   *
+                                * 1 = 16/3/1/192/4, 2 = 16/4/2/192/3,             *
+                                * 3 = 32/3/1/256/2, 4 = 16/6/4/256/2; the same    *
+                                * bits for the same list capacity, FP32 rounding  *
+                                * otherwise); the three fields above are then     *
+                                * ignored.  0: the FP32 FMA forms above           */
 } mmsar_tiles;
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the

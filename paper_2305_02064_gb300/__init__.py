@@ -89,17 +89,19 @@ class Plan:
             self._lib.mmsar_plan_destroy(h)
             self._h = None
 
-    def set_tiles(self, freqs_per_lane: int, warps_per_cta: int, grouped: int = 0):
-        """Gridding launch shape (see mmsar_plan_set_tiles; tune.autotune picks one)."""
+    def set_tiles(self, freqs_per_lane: int, warps_per_cta: int, grouped: int = 0, tensor_cores: int = 0):
+        """Gridding form and launch shape (see mmsar_plan_set_tiles; tune.autotune
+        picks one): tensor_cores=1 selects the tensor-core gridding (the other
+        fields are then ignored), else the FP32 FMA form given by the others."""
         _lib.check(self._lib.mmsar_plan_set_tiles(self._h, ctypes.byref(
-            _lib.Tiles(int(freqs_per_lane), int(warps_per_cta), int(grouped)))))
+            _lib.Tiles(int(freqs_per_lane), int(warps_per_cta), int(grouped), int(tensor_cores)))))
 
     @property
     def tiles(self):
-        """(frequencies per lane, warps per CTA, grouped) of the gridding launch."""
+        """(frequencies per lane, warps per CTA, grouped, tensor cores) of the gridding."""
         t = _lib.Tiles()
         _lib.check(self._lib.mmsar_plan_get_tiles(self._h, ctypes.byref(t)))
-        return (t.grid_freqs_per_lane, t.grid_warps_per_cta, t.grid_grouped)
+        return (t.grid_freqs_per_lane, t.grid_warps_per_cta, t.grid_grouped, t.grid_tensor_cores)
 
     @property
     def volume_shape(self):

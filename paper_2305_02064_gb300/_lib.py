@@ -56,7 +56,7 @@ class Grid(ctypes.Structure):
 
 class Tiles(ctypes.Structure):
     _fields_ = [("grid_freqs_per_lane", ctypes.c_int), ("grid_warps_per_cta", ctypes.c_int),
-                ("grid_grouped", ctypes.c_int)]
+                ("grid_grouped", ctypes.c_int), ("grid_tensor_cores", ctypes.c_int)]
 
 
 class Options(ctypes.Structure):

@@ -81,6 +81,7 @@ struct Plan {
     int spread_nf;      // gridding launch shape: frequencies per lane (1, 2 or 4)
     int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells; half as tall for 4)
     bool grouped;       // gridding by groups of samples sharing x' (else per sample)
+    int tc;             // gridding on the tensor cores, pipeline variant 1..4 (grid_tc.cu); 0: the FP32 forms above
     int64_t G;          // group slots: n_tx n_rx n_pos (every class may be a single pair)
     int64_t n_bins;
     bool zref_given;
@@ -96,6 +97,9 @@ struct Plan {
     size_t off_gdd, off_gxq; // per sorted group: (in-bin offsets, group index); x weight quads [w + 3]
     size_t off_goff;         // per sorted group: its members' y offsets, uint16 x 16
     size_t off_yq;           // per sample (original order): offset header + y weight quads [w + 4]
+    size_t off_trec;         // tensor-core gridding: per sorted sample (index, first cell, fractions)
+    size_t off_sexp;         // tensor-core gridding: per (64-frequency group, sample) normalisation exponent
+    size_t off_aref;         // tensor-core gridding: per group max of 127 - exponent (cleared per image)
     size_t off_shat, off_G, off_A, off_S, off_Z, off_B;
     size_t ws_bytes;
     // optional per-stage timing events (caller-owned)
@@ -124,6 +128,8 @@ cudaError_t launch_bin_scatter(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s);
 cudaError_t launch_spread(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_spread_groups(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_grid_tc(const Plan &p, void *ws, cudaStream_t s);
+cudaError_t launch_grid_tc_multi(const mmsar_request *r, int n, cudaStream_t s);
 cudaError_t launch_fft_x(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_fft_y(const Plan &p, void *ws, cudaStream_t s);
 cudaError_t launch_stolt(const Plan &p, void *ws, cudaStream_t s);

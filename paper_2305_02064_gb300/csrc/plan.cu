@@ -166,6 +166,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.spread_nf = 2;
     p.spread_warps = 4;   // the autotuner's choice on the realistic, large and most batched scans
     p.grouped = false;
+    p.tc = 0;             // FP32 FMA gridding (the tensor-core variants 1..4 are autotuner options)
     p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;
@@ -186,6 +187,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     };
     const size_t L = (size_t)p.L;
     p.off_partials = take(sizeof(double) * 128);
+    p.off_aref = take(sizeof(int) * 64);   // before the bin counts: cleared with the header
     p.off_counts = take(sizeof(int) * (size_t)p.n_bins);
     p.off_offsets = take(sizeof(int) * ((size_t)p.n_bins + 1));
     p.off_cursor = take(sizeof(int) * (size_t)p.n_bins);
@@ -202,6 +204,8 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.off_gxq = take(sizeof(float4) * (size_t)(p.w + 3) * (size_t)p.G);
     p.off_goff = take(2 * sizeof(int4) * (size_t)p.G);
     p.off_yq = take(sizeof(float4) * (size_t)(p.w + 4) * L);
+    p.off_trec = take(sizeof(int4) * L);
+    p.off_sexp = take((size_t)((p.n_kc + 1) / 2) * L);
     p.off_shat = take(sizeof(float2) * (size_t)((p.n_kc + 1) / 2) * L * 2 * kKC);   // 64-frequency groups
     const size_t G = sizeof(float2) * (size_t)p.n_kc * p.mry * p.mrx * kKC;
     const size_t S = sizeof(float2) * (size_t)p.mx * p.my * p.nkp;
@@ -283,9 +287,12 @@ mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
         return fail(MMSAR_ERR_INVALID_ARG, "the grouped form takes 1 or 2 frequencies per lane");
     if (tiles->grid_grouped && (int64_t)plan->p.shape.n_tx * plan->p.shape.n_rx > kMaxPairsGrouped)
         return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "grouped gridding takes at most %d Tx/Rx pairs", kMaxPairsGrouped);
+    if (tiles->grid_tensor_cores < 0 || tiles->grid_tensor_cores > 4)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_tensor_cores must be 0 .. 4");
     plan->p.spread_nf = tiles->grid_freqs_per_lane;
     plan->p.spread_warps = tiles->grid_warps_per_cta;
     plan->p.grouped = tiles->grid_grouped != 0;
+    plan->p.tc = tiles->grid_tensor_cores;
     return MMSAR_OK;
 }
 
@@ -294,6 +301,7 @@ mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles) {
     tiles->grid_freqs_per_lane = plan->p.spread_nf;
     tiles->grid_warps_per_cta = plan->p.spread_warps;
     tiles->grid_grouped = plan->p.grouped ? 1 : 0;
+    tiles->grid_tensor_cores = plan->p.tc;
     return MMSAR_OK;
 }
 
@@ -363,7 +371,9 @@ mmsar_status mmsar_image(mmsar_plan *plan, void *workspace, size_t workspace_byt
     MMSAR_MARK(1);
     MMSAR_STEP(launch_compensate(p, workspace, echo, echo_scale, s), "compensation, bin sort and gridding weights");
     MMSAR_MARK(2);
-    MMSAR_STEP(p.grouped ? launch_spread_groups(p, workspace, s) : launch_spread(p, workspace, s), "gridding");
+    MMSAR_STEP(p.tc ? launch_grid_tc(p, workspace, s)
+                    : (p.grouped ? launch_spread_groups(p, workspace, s) : launch_spread(p, workspace, s)),
+               "gridding");
     MMSAR_MARK(3);
     MMSAR_STEP(launch_fft_x(p, workspace, s), "FT_2D along x'");
     MMSAR_MARK(4);
@@ -435,6 +445,7 @@ mmsar_status mmsar_image_batch_fused(const mmsar_request *reqs, int n, void *str
     MMSAR_STEP(launch_bin_scatter_multi(r, m, s), "bin scatter");
     MMSAR_STEP(launch_compensate_multi(r, m, s), "compensation, bin sort and gridding weights");
     MMSAR_STEP(launch_spread_multi(r, m, s), "gridding");
+    MMSAR_STEP(launch_grid_tc_multi(r, m, s), "gridding on the tensor cores");
     MMSAR_STEP(launch_fft_multi(r, m, 0, s), "FT_2D along x'");
     MMSAR_STEP(launch_fft_multi(r, m, 1, s), "FT_2D along y'");
     MMSAR_STEP(launch_stolt_multi(r, m, s), "Stolt");

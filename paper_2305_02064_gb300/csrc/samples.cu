@@ -769,6 +769,24 @@ __device__ void sort_and_weigh_bin(int b, const int *__restrict__ offsets, int *
     }
 }
 
+// Tensor-core gridding: one bin in ascending sample order, and per sample in
+// that order a 16-byte record (sample index, first cell u0 | v0 << 16, cell
+// fractions fx, fy).
+__device__ void sort_and_record_bin_tc(int b, const int *__restrict__ offsets, int *__restrict__ perm,
+                                       const SampleRec *__restrict__ rec, int4 *__restrict__ trec, int *keys,
+                                       int *sorted) {
+    const int lane = threadIdx.x & 31;
+    const int beg = offsets[b], n = offsets[b + 1] - beg;
+    if (n == 0) return;
+    int *pp = perm + beg;
+    const bool small = sort_bin(pp, n, keys, sorted);
+    for (int sl = lane; sl < n; sl += 32) {
+        const int l = small ? sorted[sl] : pp[sl];
+        const SampleRec r = rec[l];
+        trec[beg + sl] = make_int4(l, (r.u0 & 0xffff) | (r.v0 << 16), __float_as_int(r.fx), __float_as_int(r.fy));
+    }
+}
+
 // -- compensation (Eq. 11)
 // One warp per group of kCompUnroll samples and one 64-frequency group g:
 // each lane reads two frequencies of each sample of the group (the loads of
@@ -846,6 +864,9 @@ struct PrepTailArgs {
     int2 *gdd;
     int4 *goff;
     float4 *gxq, *yq;
+    // tensor-core gridding: compact records (bin order) instead of the above
+    int tc;
+    int4 *trec;
     // compensation
     const void *echo;
     const float *scale;
@@ -853,20 +874,47 @@ struct PrepTailArgs {
     int Nk, L, chunk_blocks;
     int *err;
     float2 *shat;
+    // split output (tensor-core gridding): s_hat 2^a as FP16 hi / lo planes
+    // [g][L][2][128 halves] (shat reinterpreted), exponents a [g][L], and per
+    // group the max of 127 - a
+    signed char *sexp;
+    int *aref;
 };
+
+// Power-of-two normalisation of a 64-frequency row: a such that
+// m 2^a lies in [2^13, 2^14) for its largest component m (127 for an
+// all-zero row, clamped to +-120 otherwise).
+__device__ __forceinline__ int norm_exponent(float m) {
+    if (!(m > 0.f) || !isfinite(m)) return m > 0.f ? -120 : 127;
+    int e;
+    frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+    const int a = 14 - e;
+    return a < -120 ? -120 : (a > 120 ? 120 : a);
+}
+
+// FP16 hi / lo split of two values scaled by 2^a (exact scaling): (hi, lo) half2 pairs
+__device__ __forceinline__ void split2(float x, float y, float sc, __half2 &hi, __half2 &lo) {
+    const float xs = x * sc, ys = y * sc;
+    hi = __floats2half2_rn(xs, ys);
+    const float2 h = __half22float2(hi);
+    lo = __floats2half2_rn(xs - h.x, ys - h.y);
+}
 
 // VEC: lane l takes the adjacent frequencies 64 g + 2 l and 64 g + 2 l + 1
 // (one 16-byte or 8-byte load, one 16-byte store per sample; Nk even and the
 // echo aligned); otherwise 64 g + l and 64 g + 32 + l.
-template <int DT, bool VEC>
+template <int DT, bool VEC, bool SPLIT>
 __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) {
     __shared__ int keys[kPrepWarps][kSortBinCap];
     __shared__ int sorted[kPrepWarps][kSortBinCap];
+    __shared__ int amax_s[kPrepWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (bid < a.n_sort_blocks) {
         const int b = bid * kPrepWarps + warp;
         if (b < a.n_bins) {
-            if (a.grouped)
+            if (a.tc)
+                sort_and_record_bin_tc(b, a.offsets, a.perm, a.rec, a.trec, keys[warp], sorted[warp]);
+            else if (a.grouped)
                 sort_and_weigh_group_bin(b, a.offsets, a.perm, a.grec, a.w, a.kappa, a.gdd, a.gxq, a.goff, a.rec,
                                          a.cls, a.TR, a.P, a.mry, keys[warp], sorted[warp]);
             else
@@ -900,6 +948,7 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
     const int warps = a.chunk_blocks * kPrepWarps;
     const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *a.scale;
     bool bad = false;
+    int amax = 0;   // max of 127 - a over this warp's rows (split output)
     for (int g0 = (bx * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
         uint2 ph[kCompUnroll];
         float2 v[kCompUnroll][2];
@@ -919,6 +968,70 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
                                                   : make_float2(0.f, 0.f);
                 }
             }
+        }
+        if constexpr (SPLIT) {
+            // rotate, then normalise each sample's 64-frequency row by 2^a and
+            // store it as FP16 hi / lo planes (tensor-core gridding)
+            float4 o[kCompUnroll];
+            float mx[kCompUnroll];
+#pragma unroll
+            for (int u = 0; u < kCompUnroll; ++u) {
+                const int l = g0 + u;
+                o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (l < a.L) {
+                    if (VEC) {
+                        const int k0 = 64 * g + 2 * lane;
+                        if (k0 < Nk) {
+                            bad |= !(isfinite(v[u][0].x) && isfinite(v[u][0].y) && isfinite(v[u][1].x) &&
+                                     isfinite(v[u][1].y));
+                            const uint32_t t0 = ph[u].x + (uint32_t)k0 * ph[u].y;   // exact mod 2^32
+                            const float2 o0 = rotate_turns(v[u][0], t0), o1 = rotate_turns(v[u][1], t0 + ph[u].y);
+                            o[u] = make_float4(o0.x, o0.y, o1.x, o1.y);
+                        }
+                    } else {
+                        float2 oo[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int k = 64 * g + 32 * h + lane;
+                            if (k < Nk) {
+                                bad |= !(isfinite(v[u][h].x) && isfinite(v[u][h].y));
+                                oo[h] = rotate_turns(v[u][h], ph[u].x + (uint32_t)k * ph[u].y);
+                            }
+                        }
+                        o[u] = make_float4(oo[0].x, oo[0].y, oo[1].x, oo[1].y);
+                    }
+                }
+                mx[u] = fmaxf(fmaxf(fabsf(o[u].x), fabsf(o[u].y)), fmaxf(fabsf(o[u].z), fabsf(o[u].w)));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int u = 0; u < kCompUnroll; ++u) mx[u] = fmaxf(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], off));
+#pragma unroll
+            for (int u = 0; u < kCompUnroll; ++u) {
+                const int l = g0 + u;
+                if (l >= a.L) continue;
+                const int ex = norm_exponent(mx[u]);
+                amax = max(amax, 127 - ex);
+                const float sc = ldexpf(1.0f, ex);
+                __half2 h0, l0, h1, l1;
+                split2(o[u].x, o[u].y, sc, h0, l0);
+                split2(o[u].z, o[u].w, sc, h1, l1);
+                __half2 *row = reinterpret_cast<__half2 *>(a.shat) + ((long long)g * a.L + l) * 128;   // 512 B
+                if (VEC) {   // complex 2 lane, 2 lane + 1 -> halves 4 lane .. 4 lane + 3
+                    row[2 * lane] = h0;
+                    row[2 * lane + 1] = h1;
+                    row[64 + 2 * lane] = l0;
+                    row[64 + 2 * lane + 1] = l1;
+                } else {     // complex lane and 32 + lane
+                    row[lane] = h0;
+                    row[32 + lane] = h1;
+                    row[64 + lane] = l0;
+                    row[64 + 32 + lane] = l1;
+                }
+                if (lane == 0) a.sexp[(long long)g * a.L + l] = (signed char)ex;
+            }
+            continue;
         }
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
@@ -950,20 +1063,29 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
+    if constexpr (SPLIT) {   // the group's reference exponent: one atomic per block
+        if (lane == 0) amax_s[warp] = amax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int m = 0;
+            for (int i = 0; i < kPrepWarps; ++i) m = max(m, amax_s[i]);
+            if (m > 0) atomicMax(a.aref + g, m);
+        }
+    }
 }
 
-template <int DT, bool VEC>
+template <int DT, bool VEC, bool SPLIT>
 __global__ void __launch_bounds__(kPrepWarps * 32) compensate_kernel(const __grid_constant__ PrepTailArgs a) {
-    compensate_body<DT, VEC>(a, blockIdx.x);
+    compensate_body<DT, VEC, SPLIT>(a, blockIdx.x);
 }
 
-template <int DT, bool VEC>
+template <int DT, bool VEC, bool SPLIT>
 __global__ void __launch_bounds__(kPrepWarps * 32)
     compensate_multi(const __grid_constant__ BatchTable<PrepTailArgs> t) {
     __shared__ PrepTailArgs sa;
     int bid, nb;
     batch_args(t, batch_scan(t, bid, nb), &sa);
-    compensate_body<DT, VEC>(sa, bid);
+    compensate_body<DT, VEC, SPLIT>(sa, bid);
 }
 
 // the kernel instance: 2 x echo dtype + paired loads
@@ -980,8 +1102,12 @@ static int compensate_describe(const Plan &p, void *ws, const void *echo, const 
     a.kappa = (float)(1.5 * kPi / p.w);
     a.dd = reinterpret_cast<int2 *>(w + p.off_dd);
     a.wrec = reinterpret_cast<float4 *>(w + p.off_wq);
-    a.grouped = p.grouped ? 1 : 0;
-    a.n_yrec_blocks = p.grouped ? (int)((p.L * (p.w + 4) + kPrepWarps * 32 - 1) / (kPrepWarps * 32)) : 0;
+    a.tc = p.tc ? 1 : 0;
+    a.trec = reinterpret_cast<int4 *>(w + p.off_trec);
+    a.sexp = reinterpret_cast<signed char *>(w + p.off_sexp);
+    a.aref = reinterpret_cast<int *>(w + p.off_aref);
+    a.grouped = (p.grouped && !p.tc) ? 1 : 0;
+    a.n_yrec_blocks = a.grouped ? (int)((p.L * (p.w + 4) + kPrepWarps * 32 - 1) / (kPrepWarps * 32)) : 0;
     a.P = p.shape.n_pos;
     a.R = p.shape.n_rx;
     a.TR = p.shape.n_tx * p.shape.n_rx;
@@ -1006,30 +1132,44 @@ static int compensate_describe(const Plan &p, void *ws, const void *echo, const 
     // paired loads need an even Nk and an echo aligned to one pair
     const size_t pair_bytes = p.shape.dtype == MMSAR_ECHO_C64 ? 16 : 8;
     const bool vec = p.shape.n_k % 2 == 0 && reinterpret_cast<uintptr_t>(echo) % pair_bytes == 0;
-    key = 2 * (int)p.shape.dtype + (vec ? 1 : 0);
+    key = 8 * (p.tc ? 1 : 0) + 2 * (int)p.shape.dtype + (vec ? 1 : 0);
     return (int)(a.n_sort_blocks + a.n_yrec_blocks + cb * ((p.n_kc + 1) / 2));
 }
 
-template <int DT, bool VEC>
+template <int DT, bool VEC, bool SPLIT>
 static void compensate_launch(const PrepTailArgs *a, const BatchTable<PrepTailArgs> *t, int blocks, cudaStream_t s) {
     if (a)
-        compensate_kernel<DT, VEC><<<blocks, kPrepWarps * 32, 0, s>>>(*a);
+        compensate_kernel<DT, VEC, SPLIT><<<blocks, kPrepWarps * 32, 0, s>>>(*a);
     else
-        compensate_multi<DT, VEC><<<blocks, kPrepWarps * 32, 0, s>>>(*t);
+        compensate_multi<DT, VEC, SPLIT><<<blocks, kPrepWarps * 32, 0, s>>>(*t);
 }
 
+template <bool SPLIT>
+static void compensate_dispatch_dt(int key, const PrepTailArgs *a, const BatchTable<PrepTailArgs> *t, int blocks,
+                                   cudaStream_t s) {
+    switch (key & 7) {
+        case 2 * MMSAR_ECHO_C64 + 1: compensate_launch<MMSAR_ECHO_C64, true, SPLIT>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_C64: compensate_launch<MMSAR_ECHO_C64, false, SPLIT>(a, t, blocks, s); break;
+        case 2 * MMSAR_ECHO_F16X2_SCALED + 1:
+            compensate_launch<MMSAR_ECHO_F16X2_SCALED, true, SPLIT>(a, t, blocks, s);
+            break;
+        case 2 * MMSAR_ECHO_F16X2_SCALED:
+            compensate_launch<MMSAR_ECHO_F16X2_SCALED, false, SPLIT>(a, t, blocks, s);
+            break;
+        case 2 * MMSAR_ECHO_BF16X2_SCALED + 1:
+            compensate_launch<MMSAR_ECHO_BF16X2_SCALED, true, SPLIT>(a, t, blocks, s);
+            break;
+        default: compensate_launch<MMSAR_ECHO_BF16X2_SCALED, false, SPLIT>(a, t, blocks, s); break;
+    }
+}
+
+// key: 8 x split output (tensor-core gridding) + 2 x echo dtype + paired loads
 static void compensate_dispatch(int key, const PrepTailArgs *a, const BatchTable<PrepTailArgs> *t, int blocks,
                                 cudaStream_t s) {
-    switch (key) {
-        case 2 * MMSAR_ECHO_C64 + 1: compensate_launch<MMSAR_ECHO_C64, true>(a, t, blocks, s); break;
-        case 2 * MMSAR_ECHO_C64: compensate_launch<MMSAR_ECHO_C64, false>(a, t, blocks, s); break;
-        case 2 * MMSAR_ECHO_F16X2_SCALED + 1: compensate_launch<MMSAR_ECHO_F16X2_SCALED, true>(a, t, blocks, s); break;
-        case 2 * MMSAR_ECHO_F16X2_SCALED: compensate_launch<MMSAR_ECHO_F16X2_SCALED, false>(a, t, blocks, s); break;
-        case 2 * MMSAR_ECHO_BF16X2_SCALED + 1:
-            compensate_launch<MMSAR_ECHO_BF16X2_SCALED, true>(a, t, blocks, s);
-            break;
-        default: compensate_launch<MMSAR_ECHO_BF16X2_SCALED, false>(a, t, blocks, s); break;
-    }
+    if (key & 8)
+        compensate_dispatch_dt<true>(key, a, t, blocks, s);
+    else
+        compensate_dispatch_dt<false>(key, a, t, blocks, s);
 }
 
 cudaError_t launch_compensate(const Plan &p, void *ws, const void *echo, const float *scale, cudaStream_t s) {

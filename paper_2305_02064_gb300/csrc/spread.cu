@@ -631,6 +631,8 @@ cudaError_t launch_spread_multi(const mmsar_request *r, int n, cudaStream_t s) {
     for (int i = 0; i < n; ++i) {
         const Plan &p = r[i].plan->p;
         keys[i] = 2 * p.spread_nf + (p.spread_warps == 8 ? 1 : 0);
+        if (p.tc)
+            continue;   // tensor-core gridding: launch_grid_tc_multi
         if (p.grouped)
             gblocks[i] = spread_groups_describe(p, r[i].workspace, ga[i]);
         else

@@ -99,16 +99,22 @@ def test_realistic_workspace_fits_hbm():
 
 
 def test_gridding_launch_shape_setter():
-    """mmsar_plan_set_tiles accepts the gridding launch shapes and rejects
-    everything else (the grouped form takes 1 or 2 frequencies per lane); the
-    default is 64 frequencies on 4 warps, per sample."""
+    """mmsar_plan_set_tiles accepts the gridding forms and launch shapes and
+    rejects everything else (the grouped form takes 1 or 2 frequencies per
+    lane); the default is the FP32 form over 64 frequencies on 4 warps, per
+    sample."""
     from paper_2305_02064_gb300._lib import MmsarError
     p = _plan()
-    assert p.tiles == (2, 4, 0)
+    assert p.tiles == (2, 4, 0, 0)
     for shp in ((1, 4, 0), (2, 4, 1), (4, 4, 0), (1, 8, 1), (4, 8, 0), (2, 8, 0)):
         p.set_tiles(*shp)
-        assert p.tiles == shp
-    for bad in ((0, 8, 0), (3, 8, 0), (8, 4, 0), (4, 4, 1), (2, 2, 0), (2, 16, 0), (-1, 4, 0), (2, 8, 2)):
+        assert p.tiles == shp + (0,)
+    for v in (1, 2, 3, 4):
+        p.set_tiles(2, 4, 0, v)
+        assert p.tiles == (2, 4, 0, v)
+    p.set_tiles(2, 8, 0)
+    for bad in ((0, 8, 0), (3, 8, 0), (8, 4, 0), (4, 4, 1), (2, 2, 0), (2, 16, 0), (-1, 4, 0), (2, 8, 2),
+                (2, 4, 0, 5), (2, 4, 0, -1)):
         with pytest.raises(MmsarError, match="INVALID_ARG"):
             p.set_tiles(*bad)
-    assert p.tiles == (2, 8, 0)   # the last valid setting stays
+    assert p.tiles == (2, 8, 0, 0)   # the last valid setting stays

@@ -57,7 +57,7 @@ def test_fused_batch_equals_single(dev):
     from paper_2305_02064_gb300.batch import ScanJob, image_batch_fused
     scans = small_mix(8)
     jobs = [ScanJob(s, dev, dtype="f16" if i % 3 == 2 else "c64") for i, s in enumerate(scans)]
-    shapes = [(2, 4, 0), (1, 8, 0), (2, 8, 1), (4, 4, 0), (1, 4, 0), (4, 8, 0)]
+    shapes = [(2, 4, 0, 2), (1, 8, 0), (2, 8, 1), (4, 4, 0), (2, 4, 0, 3), (4, 8, 0)]
     for i, j in enumerate(jobs):
         j.plan.set_tiles(*shapes[i % len(shapes)])
     single = []
@@ -142,22 +142,35 @@ def test_graph_replay_equals_eager(dev):
 
 @pytest.mark.parametrize("dtype", ["c64", "f16"])
 def test_server_alone_and_in_the_mix(dev, dtype):
+    """Served requests give the same volume alone and in the mix.  The
+    device arena holds fewer requests than there are slots (the cap is under
+    slots x the largest footprint), so admission queues on memory; nothing
+    is allocated on the device while serving."""
     from paper_2305_02064_gb300.serve import GpuExecutor, Scheduler, ServeRequest, latency_summary
     scans = small_mix(8)
-    ex_alone = GpuExecutor(dev, dtype=dtype, n_streams=1, keep_results=True)
+    probe = GpuExecutor(dev, dtype=dtype, n_streams=1, mem_cap=1 << 20)
+    biggest = max(probe.footprint(s) for s in scans)
+    del probe
+    ex_alone = GpuExecutor(dev, dtype=dtype, n_streams=1, keep_results=True, mem_cap=biggest)
     alone = {}
     for i, s in enumerate(scans):
         r = ServeRequest(i, s, 0.0, footprint=ex_alone.footprint(s))
-        Scheduler(ex_alone, slots=1, mem_cap=1 << 40).run([r])
+        Scheduler(ex_alone, slots=1, mem_cap=biggest).run([r])
         alone[i] = r.result.numpy()
-    ex = GpuExecutor(dev, dtype=dtype, n_streams=4, keep_results=True)
-    reqs = [ServeRequest(i, s, 0.002 * i, footprint=ex.footprint(s)) for i, s in enumerate(scans)]
+    cap = 2 * biggest + biggest // 2
+    ex = GpuExecutor(dev, dtype=dtype, n_streams=4, keep_results=True, mem_cap=cap)
+    reqs = [ServeRequest(i, s, 0.0, footprint=ex.footprint(s)) for i, s in enumerate(scans)]
     for r in reqs:
         ex.pin(r)
-    cap = 3 * max(r.footprint for r in reqs)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
     sch = Scheduler(ex, slots=4, mem_cap=cap)
     done = sch.run(reqs)
-    assert len(done) == len(scans) and sch.peak_in_use <= cap
+    torch.cuda.synchronize()
+    assert torch.cuda.max_memory_allocated() == alloc0   # the arena predates serving
+    assert len(done) == len(scans) and ex.arena.peak <= cap and ex.arena.in_use == 0
+    assert sch.max_concurrent < 4                        # memory, not slots, limited concurrency
     for r in done:
         assert np.array_equal(r.result.numpy().view(np.uint32), alone[r.rid].view(np.uint32))
         if dtype == "c64":

@@ -42,11 +42,32 @@ def test_deepest_z_grids(dev, nz):
     assert_parity(got, exact(scan), plan.kernel_width)
 
 
+TC = (2, 4, 0, 2)   # tensor-core gridding
+
+
+def run_with(scan, dev, tiles=None, **plan_kw):
+    """run_gpu with an explicit gridding form."""
+    if tiles is None:
+        return run_gpu(scan, dev, **plan_kw)
+    from paper_2305_02064_gb300 import Plan
+    plan = Plan.for_scan(scan, **plan_kw)
+    plan.set_tiles(*tiles)
+    ws = plan.new_workspace(dev)
+    vol = torch.full(plan.volume_shape, complex(np.nan, np.nan), dtype=torch.complex64, device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    plan.image(ws, t(scan.echo), t(np.asarray(scan.pos, np.float64)), t(np.asarray(scan.tx, np.float64)),
+               t(np.asarray(scan.rx, np.float64)), vol)
+    plan.poll_error(ws)
+    return vol.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
 @pytest.mark.parametrize("nk", [1024, 1000, 1023])
-def test_largest_frequency_counts(dev, nk):
-    """Nk at the limit (1024), below it (1000, even), odd and ragged (1023)."""
+def test_largest_frequency_counts(dev, nk, tiles):
+    """Nk at the limit (1024: sixteen 64-frequency groups), below it (1000,
+    even), odd and ragged (1023), for both gridding forms."""
     scan = synth.custom(nx_pos=4, ny_pos=4, nk=nk, layout="tiny", nx=16, ny=16, nz=8, seed=nk, snr_db=30)
-    got, plan = run_gpu(scan, dev)
+    got, plan = run_with(scan, dev, tiles)
     assert_parity(got, exact(scan), plan.kernel_width)
 
 
@@ -59,11 +80,13 @@ def test_too_many_frequencies_are_refused(dev):
         Plan(1, 2, 16, 32, 77e9, 1e8, synth.centred_grid(16, 16, 257, 1e-3, 5e-3, 0.26))
 
 
-def test_largest_spectral_grid_on_both_axes(dev):
+@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
+def test_largest_spectral_grid_on_both_axes(dev, tiles):
     """Mx = My = 1024 (the plan's largest) on a small voxel grid: 2048-point
-    FFTs along x' and y', 1024-point inverse FFTs along k_y and k_x."""
+    FFTs along x' and y', 1024-point inverse FFTs along k_y and k_x, a
+    2048 x 2048 gridding grid."""
     scan = synth.custom(nx_pos=4, ny_pos=4, nk=8, layout="tiny", nx=24, ny=20, nz=6, seed=41, jitter=(0.5e-3, 1e-3))
-    got, plan = run_gpu(scan, dev, mx=1024, my=1024)
+    got, plan = run_with(scan, dev, tiles, mx=1024, my=1024)
     assert (plan.mx, plan.my) == (1024, 1024)
     ref = rma.rma_exact(rma.setup_from(scan, Mx=1024, My=1024))
     assert_parity(got, ref, plan.kernel_width)
@@ -94,10 +117,11 @@ def multi_tile():
     return scan, rma.rma_fast(rma.setup_from(scan), w=16)
 
 
+@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
 @pytest.mark.parametrize("tol,w", [(1e-4, 8), (1e-5, 10), (1e-6, 12)])
-def test_wide_kernels_on_many_tiles(dev, multi_tile, tol, w):
+def test_wide_kernels_on_many_tiles(dev, multi_tile, tol, w, tiles):
     scan, ref = multi_tile
-    got, plan = run_gpu(scan, dev, nufft_tol=tol)
+    got, plan = run_with(scan, dev, tiles, nufft_tol=tol)
     assert plan.kernel_width == w
     e = assert_parity(got, ref, w, contract=CONTRACT)
     assert e <= BOUND_WIDE[w], (e, w)

@@ -314,7 +314,7 @@ def test_gridding_launch_shapes_are_bit_identical(dev):
                         jitter=(0.7e-3, 3e-3), snr_db=25)
     from paper_2305_02064_gb300 import Plan
     vols = {}
-    for shp in ((2, 8), (1, 8), (2, 4), (1, 4), (4, 8), (4, 4)):
+    for shp in ((2, 8), (1, 8), (2, 4), (1, 4), (4, 8), (4, 4)):   # the FP32 FMA forms
         plan = Plan.for_scan(scan)
         plan.set_tiles(*shp)
         ws = plan.new_workspace(dev)
@@ -400,3 +400,124 @@ def test_autotune_picks_a_shape_and_keeps_the_image(dev, tiny_scan):
     job.image()
     torch.cuda.synchronize()
     assert_parity(job.vol.cpu().numpy(), oracle_of(tiny_scan), 6)
+
+
+# ----------------------------------------------------------------------------- tensor-core gridding
+# The tensor-core gridding (FP16 hi/lo operands, FP32 accumulation; plan
+# option grid_tensor_cores = 1..4) against the FP32 FMA form that the tests
+# above exercise, and against the oracle.  The two compute the same sums to
+# FP32 rounding: NMSE between them <= 1e-10 (three transforms of ~2^-22
+# relative error per term give ~1e-13; the margin covers summation order).
+TC_FORM = (2, 4, 0, 2)
+FP32_FORM = (2, 4, 0, 0)
+TC_VS_FP32 = 1e-10
+
+
+def image_with(scan, dev, tiles, echo=None, dtype="c64", **plan_kw):
+    from paper_2305_02064_gb300 import Plan, quantize_echo
+    plan = Plan.for_scan(scan, dtype=dtype, **plan_kw)
+    plan.set_tiles(*tiles)
+    ws = plan.new_workspace(dev)
+    vol = torch.full(plan.volume_shape, complex(np.nan, np.nan), dtype=torch.complex64, device=dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    e = t(scan.echo if echo is None else echo)
+    scale = None
+    if dtype != "c64":
+        e, scale = quantize_echo(e, dtype)
+    plan.image(ws, e, t(np.asarray(scan.pos, np.float64)), t(np.asarray(scan.tx, np.float64)),
+               t(np.asarray(scan.rx, np.float64)), vol, echo_scale=scale)
+    plan.poll_error(ws)
+    return vol.cpu().numpy(), plan
+
+
+TC_CASES = {
+    "ragged": dict(nx_pos=7, ny_pos=5, nk=20, layout="awr1443", nx=24, ny=12, nz=10, seed=9, jitter=(0.7e-3, 4e-3),
+                   snr_db=20),
+    "many_tiles": dict(nx_pos=40, ny_pos=36, nk=48, layout="awr1443", nx=64, ny=64, nz=24, dz=4e-3, z0=0.24, seed=21,
+                       serp=True, jitter=(1.5e-3, 3e-3), n_points=6),
+    "three_chunks": dict(nx_pos=12, ny_pos=10, nk=96, layout="3x4", nx=32, ny=24, nz=12, seed=4, snr_db=30),
+    "odd_nk": dict(nx_pos=9, ny_pos=8, nk=33, layout="tiny", nx=32, ny=16, nz=12, seed=33, snr_db=25),
+}
+
+
+@pytest.mark.parametrize("case", sorted(TC_CASES))
+@pytest.mark.parametrize("plan_kw", [{}, {"nufft_tol": 1e-6}, {"compensate": 2}], ids=["w6", "w12", "mode2"])
+def test_tensor_core_gridding_matches_fp32_form(dev, case, plan_kw):
+    scan = synth.custom(**TC_CASES[case])
+    tc, plan = image_with(scan, dev, TC_FORM, **plan_kw)
+    fp, _ = image_with(scan, dev, FP32_FORM, **plan_kw)
+    assert np.all(np.isfinite(tc))
+    assert rma.nmse(tc, fp) <= TC_VS_FP32, rma.nmse(tc, fp)
+    assert rma.peak_index(tc) == rma.peak_index(fp)
+    ref = rma.rma_fast(rma.setup_from(scan, compensate=plan_kw.get("compensate", 1)), w=16)
+    assert rma.nmse(tc, ref) <= BOUND.get(plan.kernel_width, 1e-8)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_tensor_core_gridding_reduced_storage(dev, dtype):
+    scan = synth.custom(**TC_CASES["many_tiles"])
+    tc, _ = image_with(scan, dev, TC_FORM, dtype=dtype)
+    fp, _ = image_with(scan, dev, FP32_FORM, dtype=dtype)
+    assert rma.nmse(tc, fp) <= TC_VS_FP32
+
+
+def test_tensor_core_dense_tiles(dev):
+    """Positions at a quarter of the grid pitch: thousands of samples reach
+    each 8 x 8-cell tile, so the per-tile list runs in several passes into
+    the same accumulator."""
+    scan = synth.custom(nx_pos=48, ny_pos=40, nk=24, layout="awr1443", nx=16, ny=16, nz=8, dx=4e-3, seed=17,
+                        jitter=(0.3e-3, 1e-3), n_points=3)
+    tc, plan = image_with(scan, dev, TC_FORM)
+    fp, _ = image_with(scan, dev, FP32_FORM)
+    assert rma.nmse(tc, fp) <= TC_VS_FP32
+    assert_parity(tc, oracle_of(scan), plan.kernel_width)
+
+
+def test_tensor_core_empty_tiles_inside_the_window(dev):
+    """Two clusters of positions far apart: the occupied window spans the gap,
+    whose tiles list no sample and must come out zero."""
+    a = synth.custom(nx_pos=6, ny_pos=5, nk=16, layout="awr1443", nx=64, ny=32, nz=8, seed=5, n_points=2)
+    pos = np.concatenate([np.asarray(a.pos) + [-0.022, 0, 0], np.asarray(a.pos) + [0.022, 0, 0]])
+    echo = synth.echo(pos, a.tx, a.rx, a.f0, a.df, 16, a.scatterers)
+    scan = dataclasses.replace(a, pos=pos, echo=echo)
+    tc, plan = image_with(scan, dev, TC_FORM)
+    fp, _ = image_with(scan, dev, FP32_FORM)
+    assert rma.nmse(tc, fp) <= TC_VS_FP32
+    assert_parity(tc, oracle_of(scan), plan.kernel_width)
+
+
+def test_tensor_core_extreme_magnitudes(dev):
+    """The per-row power-of-two normalisation keeps FP32 accuracy over the
+    FP32 range: the image scales linearly from 1e-30 to 1e30, and samples of
+    very different magnitudes in one scan still agree with the FP32 form."""
+    scan = synth.custom(**TC_CASES["ragged"])
+    base, _ = image_with(scan, dev, TC_FORM)
+    for f in (1e-30, 1e30):
+        v, _ = image_with(scan, dev, TC_FORM, echo=(scan.echo * np.float32(f)).astype(np.complex64))
+        assert rma.nmse(v / f, base) <= TC_VS_FP32, f
+    mixed = scan.echo.copy()
+    mixed[:, :, ::2] *= np.float32(1e6)
+    tc, _ = image_with(scan, dev, TC_FORM, echo=mixed)
+    fp, _ = image_with(scan, dev, FP32_FORM, echo=mixed)
+    assert rma.nmse(tc, fp) <= TC_VS_FP32
+
+
+def test_tensor_core_zero_echo(dev):
+    scan = synth.custom(**TC_CASES["ragged"])
+    v, _ = image_with(scan, dev, TC_FORM, echo=np.zeros_like(scan.echo))
+    assert np.all(v == 0)
+
+
+def test_tensor_core_gridding_is_deterministic(dev):
+    """The same bits on every run, and for every pipeline variant with the
+    same list capacity (the same listed order and the same chain of K = 16
+    steps, only scheduled differently: variants 1-2 list 192 samples per
+    pass, 3-4 list 256); across capacities the steps regroup at the pass
+    boundaries and the images agree to FP32 rounding."""
+    scan = synth.custom(**TC_CASES["many_tiles"])
+    vols = {v: image_with(scan, dev, (2, 4, 0, v))[0] for v in (1, 2, 3, 4)}
+    again = image_with(scan, dev, TC_FORM)[0]
+    assert np.array_equal(again.view(np.uint64), vols[TC_FORM[3]].view(np.uint64))
+    assert np.array_equal(vols[1].view(np.uint64), vols[2].view(np.uint64))
+    assert np.array_equal(vols[3].view(np.uint64), vols[4].view(np.uint64))
+    assert rma.nmse(vols[1], vols[3]) <= TC_VS_FP32

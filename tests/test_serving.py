@@ -3,7 +3,7 @@ executor (no GPU): memory admission, slot limits, arrival order and latency
 accounting."""
 import pytest
 
-from paper_2305_02064_gb300.serve import Scheduler, ServeRequest, latency_summary, poisson_arrivals
+from paper_2305_02064_gb300.serve import Arena, Scheduler, ServeRequest, latency_summary, poisson_arrivals
 
 
 class FakeClock:
@@ -107,3 +107,43 @@ def test_plan_cache_is_bounded_and_shares_plans(monkeypatch):
     assert len(batch._PLAN_CACHE) == 3
     assert batch.plan_for(scans[0]) is not p0        # evicted, rebuilt
     batch._PLAN_CACHE.clear()
+
+
+def test_arena_first_fit_all_or_nothing_and_merging():
+    a = Arena(4096, align=256)
+    p1 = a.place([100, 600])            # rounded to 256, 768
+    assert p1 == [(0, 256), (256, 768)] and a.in_use == 1024
+    p2 = a.place([2048])
+    assert p2 == [(1024, 2048)]
+    assert a.place([512, 1024]) is None  # 1024 left: the second block does not fit -> nothing placed
+    assert a.in_use == 3072 and a.largest_free() == 1024
+    a.release(p1)
+    assert a.free == [(0, 1024), (3072, 1024)]
+    a.release(p2)
+    assert a.free == [(0, 4096)] and a.in_use == 0 and a.peak == 3072
+
+
+class BlockExecutor(FakeExecutor):
+    """A fake executor whose requests need device blocks of given sizes."""
+
+    def __init__(self, clock, work, arena):
+        super().__init__(clock, work)
+        self.arena = arena
+
+    def block_sizes(self, req):
+        return req.scan
+
+
+def test_scheduler_admits_by_arena_placement():
+    """Requests wait until the arena can place all their blocks, whatever
+    the footprints add up to; fragmentation is handled by first fit."""
+    clk = FakeClock()
+    arena = Arena(1000, align=1)
+    ex = BlockExecutor(clk, work=20, arena=arena)
+    reqs = [ServeRequest(i, [300, 100], arrival=0.0, footprint=0) for i in range(5)]
+    sch = Scheduler(ex, slots=8, mem_cap=10 ** 9, clock=clk)
+    done = sch.run(reqs)
+    assert len(done) == 5 and ex.max_live == 2      # 2 x 400 <= 1000 < 3 x 400
+    assert arena.peak <= 1000 and arena.in_use == 0 and arena.free == [(0, 1000)]
+    with pytest.raises(ValueError):
+        Scheduler(ex, slots=2, mem_cap=10 ** 9, clock=clk).run([ServeRequest(9, [600, 500], 0.0)])
