@@ -140,13 +140,14 @@ typedef struct {
                                 * a per-tile product weights x samples, FP32-     *
                                 * accurate (FP16 hi/lo operands, FP32             *
                                 * accumulation); the value picks the pipeline     *
-                                * (samples per MMA chunk / stages / chunks        *
-                                * gathered ahead / list capacity / CTAs per SM:   *
-                                * 1 = 16/3/1/192/4, 2 = 16/4/2/192/3,             *
-                                * 3 = 32/3/1/256/2, 4 = 16/6/4/256/2; the same    *
-                                * bits for the same list capacity, FP32 rounding  *
-                                * otherwise); the three fields above are then     *
-                                * ignored.  0: the FP32 FMA forms above           */
+                                * (frequency groups of 64 per work item / stages /*
+                                * chunks gathered ahead / samples listed per pass *
+                                * / threads / CTAs per SM: 1 = 4/3/1/256/256/1,   *
+                                * 2 = 4/2/1/256/256/2, 3 = 2/4/2/256/256/2,       *
+                                * 4 = 1/3/1/192/128/3; the same bits for the same *
+                                * list capacity, FP32 rounding otherwise); the    *
+                                * three fields above are then ignored.  0: the    *
+                                * FP32 FMA forms above                            */
 } mmsar_tiles;
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the

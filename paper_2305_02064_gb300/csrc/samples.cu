@@ -875,15 +875,15 @@ struct PrepTailArgs {
     int *err;
     float2 *shat;
     // split output (tensor-core gridding): s_hat 2^a as FP16 hi / lo planes
-    // [g][L][2][128 halves] (shat reinterpreted), exponents a [g][L], and per
-    // group the max of 127 - a
+    // [g][L][2][128 halves] (shat reinterpreted), one exponent a per sample
+    // [L], and the max of 127 - a over all samples (one int)
     signed char *sexp;
     int *aref;
 };
 
-// Power-of-two normalisation of a 64-frequency row: a such that
-// m 2^a lies in [2^13, 2^14) for its largest component m (127 for an
-// all-zero row, clamped to +-120 otherwise).
+// Power-of-two normalisation of a sample's row: a such that m 2^a lies in
+// [2^13, 2^14) for its largest magnitude m (127 for an all-zero row, clamped
+// to +-120 otherwise).
 __device__ __forceinline__ int norm_exponent(float m) {
     if (!(m > 0.f) || !isfinite(m)) return m > 0.f ? -120 : 127;
     int e;
@@ -903,11 +903,13 @@ __device__ __forceinline__ void split2(float x, float y, float sc, __half2 &hi, 
 // VEC: lane l takes the adjacent frequencies 64 g + 2 l and 64 g + 2 l + 1
 // (one 16-byte or 8-byte load, one 16-byte store per sample; Nk even and the
 // echo aligned); otherwise 64 g + l and 64 g + 32 + l.
+template <int DT, bool VEC>
+__device__ __forceinline__ void compensate_split_body(const PrepTailArgs &a, int cblk);
+
 template <int DT, bool VEC, bool SPLIT>
 __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) {
     __shared__ int keys[kPrepWarps][kSortBinCap];
     __shared__ int sorted[kPrepWarps][kSortBinCap];
-    __shared__ int amax_s[kPrepWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (bid < a.n_sort_blocks) {
         const int b = bid * kPrepWarps + warp;
@@ -943,12 +945,15 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
         return;
     }
     const int cblk = bid - a.n_sort_blocks - a.n_yrec_blocks;
+    if constexpr (SPLIT) {
+        compensate_split_body<DT, VEC>(a, cblk);
+        return;
+    }
     const int g = cblk / a.chunk_blocks, bx = cblk - g * a.chunk_blocks;
     const int Nk = a.Nk;
     const int warps = a.chunk_blocks * kPrepWarps;
     const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *a.scale;
     bool bad = false;
-    int amax = 0;   // max of 127 - a over this warp's rows (split output)
     for (int g0 = (bx * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
         uint2 ph[kCompUnroll];
         float2 v[kCompUnroll][2];
@@ -968,70 +973,6 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
                                                   : make_float2(0.f, 0.f);
                 }
             }
-        }
-        if constexpr (SPLIT) {
-            // rotate, then normalise each sample's 64-frequency row by 2^a and
-            // store it as FP16 hi / lo planes (tensor-core gridding)
-            float4 o[kCompUnroll];
-            float mx[kCompUnroll];
-#pragma unroll
-            for (int u = 0; u < kCompUnroll; ++u) {
-                const int l = g0 + u;
-                o[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (l < a.L) {
-                    if (VEC) {
-                        const int k0 = 64 * g + 2 * lane;
-                        if (k0 < Nk) {
-                            bad |= !(isfinite(v[u][0].x) && isfinite(v[u][0].y) && isfinite(v[u][1].x) &&
-                                     isfinite(v[u][1].y));
-                            const uint32_t t0 = ph[u].x + (uint32_t)k0 * ph[u].y;   // exact mod 2^32
-                            const float2 o0 = rotate_turns(v[u][0], t0), o1 = rotate_turns(v[u][1], t0 + ph[u].y);
-                            o[u] = make_float4(o0.x, o0.y, o1.x, o1.y);
-                        }
-                    } else {
-                        float2 oo[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int k = 64 * g + 32 * h + lane;
-                            if (k < Nk) {
-                                bad |= !(isfinite(v[u][h].x) && isfinite(v[u][h].y));
-                                oo[h] = rotate_turns(v[u][h], ph[u].x + (uint32_t)k * ph[u].y);
-                            }
-                        }
-                        o[u] = make_float4(oo[0].x, oo[0].y, oo[1].x, oo[1].y);
-                    }
-                }
-                mx[u] = fmaxf(fmaxf(fabsf(o[u].x), fabsf(o[u].y)), fmaxf(fabsf(o[u].z), fabsf(o[u].w)));
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int u = 0; u < kCompUnroll; ++u) mx[u] = fmaxf(mx[u], __shfl_xor_sync(0xffffffffu, mx[u], off));
-#pragma unroll
-            for (int u = 0; u < kCompUnroll; ++u) {
-                const int l = g0 + u;
-                if (l >= a.L) continue;
-                const int ex = norm_exponent(mx[u]);
-                amax = max(amax, 127 - ex);
-                const float sc = ldexpf(1.0f, ex);
-                __half2 h0, l0, h1, l1;
-                split2(o[u].x, o[u].y, sc, h0, l0);
-                split2(o[u].z, o[u].w, sc, h1, l1);
-                __half2 *row = reinterpret_cast<__half2 *>(a.shat) + ((long long)g * a.L + l) * 128;   // 512 B
-                if (VEC) {   // complex 2 lane, 2 lane + 1 -> halves 4 lane .. 4 lane + 3
-                    row[2 * lane] = h0;
-                    row[2 * lane + 1] = h1;
-                    row[64 + 2 * lane] = l0;
-                    row[64 + 2 * lane + 1] = l1;
-                } else {     // complex lane and 32 + lane
-                    row[lane] = h0;
-                    row[32 + lane] = h1;
-                    row[64 + lane] = l0;
-                    row[64 + 32 + lane] = l1;
-                }
-                if (lane == 0) a.sexp[(long long)g * a.L + l] = (signed char)ex;
-            }
-            continue;
         }
 #pragma unroll
         for (int u = 0; u < kCompUnroll; ++u) {
@@ -1063,14 +1004,117 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
-    if constexpr (SPLIT) {   // the group's reference exponent: one atomic per block
-        if (lane == 0) amax_s[warp] = amax;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int m = 0;
-            for (int i = 0; i < kPrepWarps; ++i) m = max(m, amax_s[i]);
-            if (m > 0) atomicMax(a.aref + g, m);
+}
+
+// Split output (tensor-core gridding): one warp per group of kCompUnroll
+// samples and all their frequencies, in two passes.  Pass 1 bounds each
+// sample's |s| over all frequencies by sqrt(2) max(|Re s|, |Im s|) (the
+// rotation of Eq. 11 keeps |s|, so the echo gives it; every component of
+// s_hat is at most that); the sample's exponent a puts the bound in
+// [2^13, 2^14).  Pass 2 rotates (Eq. 11),
+// scales by 2^a (exact) and stores every 64-frequency group as FP16 hi / lo
+// planes: s_hat[g][l] = (hi[128 halves], lo[128 halves]).  The exponents
+// go to sexp[l]; aref (one int) receives the max of 127 - a.  The second
+// pass re-reads the warp's echo rows, which the first pass left in cache.
+template <int DT, bool VEC>
+__device__ __forceinline__ void compensate_split_body(const PrepTailArgs &a, int cblk) {
+    __shared__ int amax_s[kPrepWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Nk = a.Nk, n_g = (((Nk + 31) >> 5) + 1) >> 1;
+    const int warps = a.chunk_blocks * kPrepWarps;
+    const float scale = (DT == MMSAR_ECHO_C64) ? 1.0f : *a.scale;
+    bool bad = false;
+    int amax = 0;
+    for (int g0 = (cblk * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
+        uint2 ph[kCompUnroll];
+        float mc[kCompUnroll];   // largest |Re s|, |Im s| of each sample (this lane's frequencies, then the warp's)
+#pragma unroll
+        for (int u = 0; u < kCompUnroll; ++u) {
+            const int l = g0 + u;
+            ph[u] = l < a.L ? __ldg(a.phase + l) : make_uint2(0u, 0u);
+            mc[u] = 0.f;
         }
+        // pass 1
+        for (int g = 0; g < n_g; ++g) {
+#pragma unroll
+            for (int u = 0; u < kCompUnroll; ++u) {
+                const int l = g0 + u;
+                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+                if (VEC) {
+                    const int k0 = 64 * g + 2 * lane;
+                    if (l < a.L && k0 < Nk) load_echo2<DT>(a.echo, ((long long)l * Nk + k0) >> 1, scale, v0, v1);
+                } else {
+                    const int k = 64 * g + lane;
+                    if (l < a.L && k < Nk) v0 = load_echo<DT>(a.echo, (long long)l * Nk + k, scale);
+                    if (l < a.L && k + 32 < Nk) v1 = load_echo<DT>(a.echo, (long long)l * Nk + k + 32, scale);
+                }
+                bad |= !(isfinite(v0.x) && isfinite(v0.y) && isfinite(v1.x) && isfinite(v1.y));
+                mc[u] = fmaxf(mc[u], fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v1.x), fabsf(v1.y))));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < kCompUnroll; ++u) mc[u] = fmaxf(mc[u], __shfl_xor_sync(0xffffffffu, mc[u], off));
+        int ex[kCompUnroll];
+        float sc[kCompUnroll];
+#pragma unroll
+        for (int u = 0; u < kCompUnroll; ++u) {
+            // every component of s_hat is at most |s| <= sqrt(2) max(|Re s|, |Im s|)
+            // (bound rounded up; no squares, so no overflow)
+            ex[u] = norm_exponent(mc[u] * 1.4142144f);
+            sc[u] = ldexpf(1.0f, ex[u]);
+            if (g0 + u < a.L) amax = max(amax, 127 - ex[u]);
+        }
+        // pass 2
+        for (int g = 0; g < n_g; ++g) {
+#pragma unroll
+            for (int u = 0; u < kCompUnroll; ++u) {
+                const int l = g0 + u;
+                if (l >= a.L) continue;
+                float2 o0 = make_float2(0.f, 0.f), o1 = o0;
+                if (VEC) {
+                    const int k0 = 64 * g + 2 * lane;
+                    if (k0 < Nk) {
+                        float2 v0, v1;
+                        load_echo2<DT>(a.echo, ((long long)l * Nk + k0) >> 1, scale, v0, v1);
+                        const uint32_t t0 = ph[u].x + (uint32_t)k0 * ph[u].y;   // exact mod 2^32
+                        o0 = rotate_turns(v0, t0);
+                        o1 = rotate_turns(v1, t0 + ph[u].y);
+                    }
+                } else {
+                    const int k = 64 * g + lane;
+                    if (k < Nk) o0 = rotate_turns(load_echo<DT>(a.echo, (long long)l * Nk + k, scale),
+                                                  ph[u].x + (uint32_t)k * ph[u].y);
+                    if (k + 32 < Nk) o1 = rotate_turns(load_echo<DT>(a.echo, (long long)l * Nk + k + 32, scale),
+                                                       ph[u].x + (uint32_t)(k + 32) * ph[u].y);
+                }
+                __half2 h0, l0, h1, l1;
+                split2(o0.x, o0.y, sc[u], h0, l0);
+                split2(o1.x, o1.y, sc[u], h1, l1);
+                __half2 *row = reinterpret_cast<__half2 *>(a.shat) + ((long long)g * a.L + l) * 128;   // 512 B
+                if (VEC) {   // complex 2 lane, 2 lane + 1 -> halves 4 lane .. 4 lane + 3
+                    row[2 * lane] = h0;
+                    row[2 * lane + 1] = h1;
+                    row[64 + 2 * lane] = l0;
+                    row[64 + 2 * lane + 1] = l1;
+                } else {     // complex lane and 32 + lane
+                    row[lane] = h0;
+                    row[32 + lane] = h1;
+                    row[64 + lane] = l0;
+                    row[64 + 32 + lane] = l1;
+                }
+            }
+        }
+        if (lane < kCompUnroll && g0 + lane < a.L) a.sexp[g0 + lane] = (signed char)ex[lane];
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonfinite);
+    if (lane == 0) amax_s[warp] = amax;   // the reference exponent: one atomic per block
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int i = 0; i < kPrepWarps; ++i) m = max(m, amax_s[i]);
+        if (m > 0) atomicMax(a.aref, m);
     }
 }
 
@@ -1133,7 +1177,9 @@ static int compensate_describe(const Plan &p, void *ws, const void *echo, const 
     const size_t pair_bytes = p.shape.dtype == MMSAR_ECHO_C64 ? 16 : 8;
     const bool vec = p.shape.n_k % 2 == 0 && reinterpret_cast<uintptr_t>(echo) % pair_bytes == 0;
     key = 8 * (p.tc ? 1 : 0) + 2 * (int)p.shape.dtype + (vec ? 1 : 0);
-    return (int)(a.n_sort_blocks + a.n_yrec_blocks + cb * ((p.n_kc + 1) / 2));
+    // the split output covers every frequency group per warp (one exponent
+    // per sample); the complex64 output runs one block range per group
+    return (int)(a.n_sort_blocks + a.n_yrec_blocks + cb * (p.tc ? 1 : (p.n_kc + 1) / 2));
 }
 
 template <int DT, bool VEC, bool SPLIT>
