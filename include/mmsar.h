@@ -139,15 +139,13 @@ typedef struct {
     int grid_tensor_cores;     /* 1 .. 4: the gridding runs on the tensor cores as *
                                 * a per-tile product weights x samples, FP32-     *
                                 * accurate (FP16 hi/lo operands, FP32             *
-                                * accumulation); the value picks the pipeline     *
-                                * (frequency groups of 64 per work item / stages /*
-                                * chunks gathered ahead / samples listed per pass *
-                                * / threads / CTAs per SM: 1 = 4/3/1/256/256/1,   *
-                                * 2 = 4/2/1/256/256/2, 3 = 2/4/2/256/256/2,       *
-                                * 4 = 1/3/1/192/128/3; the same bits for the same *
-                                * list capacity, FP32 rounding otherwise); the    *
-                                * three fields above are then ignored.  0: the    *
-                                * FP32 FMA forms above                            */
+                                * accumulation); the value picks the pipeline:    *
+                                * 64-frequency groups per work item 4 (1, 2) or   *
+                                * 2 (3, 4); the sample rows staged through        *
+                                * registers (1, 4) or by asynchronous copies with *
+                                * two (2) or four (3) shared-memory stages; all   *
+                                * give the same bits; the three fields above are  *
+                                * then ignored.  0: the FP32 FMA forms above      */
 } mmsar_tiles;
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the

@@ -75,9 +75,14 @@ constexpr int kTcMaxRanges = 16;
 // SM.  Per stage: A (S^T) hi, lo of each group = 16 M-blocks x CH samples x
 // 16 B; B (W^T) hi, lo = 8 cell rows x CH samples x 16 B, shared by the
 // groups.
-template <int CH_, int NST_, int P_, int CAP_, int GB_, int T_, int MINB_>
+template <int CH_, int NST_, int P_, int CAP_, int GB_, int T_, int MINB_, bool REG_ = false>
 struct TcCfg {
     static constexpr int CH = CH_, NST = NST_, P = P_, CAP = CAP_, GB = GB_, T = T_, MINB = MINB_;
+    // REG: the rows of chunk q + 1 are loaded into registers while chunk q is
+    // prepared and stored to its stage at the start of the next iteration
+    // (P is then 1: one chunk ahead, held in registers, not in a stage)
+    static constexpr bool REG = REG_;
+    static constexpr int PIECES = GB * CH * 32 / T;   // 16-byte pieces per thread and chunk
     static constexpr int W = T / 32;   // warps
     static_assert(CH == 16 || CH == 32, "one or two K steps per chunk");
     static_assert(P >= 1 && P + 1 <= NST && NST <= 8, "stages");
@@ -95,10 +100,10 @@ struct TcCfg {
     static constexpr int TmemCols = 64 * GB;
 };
 // the variants the plan selects (mmsar_tiles.grid_tensor_cores = 1 .. 4)
-using TcCfg1 = TcCfg<16, 3, 1, 256, 4, 256, 1>;
+using TcCfg1 = TcCfg<16, 2, 1, 256, 4, 256, 2, true>;
 using TcCfg2 = TcCfg<16, 2, 1, 256, 4, 256, 2>;
 using TcCfg3 = TcCfg<16, 4, 2, 256, 2, 256, 2>;
-using TcCfg4 = TcCfg<16, 3, 1, 192, 1, 128, 3>;
+using TcCfg4 = TcCfg<16, 2, 1, 256, 2, 256, 2, true>;
 constexpr int kTcMaxThreads = 256;
 constexpr long long kTcWaitCycles = 1000000000ll;   // ~0.5 s at 2 GHz
 
@@ -290,6 +295,38 @@ __device__ __forceinline__ void grid_tc_item(const GridTcArgs &a, int g0, int ng
             cp_async16(st + gl * C::AGroup + plane * C::APlane + mi * (CH * 16) + j * 16, src);
         }
     };
+    // register-staged form of the same gather: this thread's pieces of
+    // listed samples [base, base + CH) into stg (coalesced 16-byte loads),
+    // then from stg into stage s
+    auto load_rows = [&](uint4 *stg, int base, int n) {
+        constexpr int PER = CH;
+#pragma unroll
+        for (int r = 0; r < C::PIECES; ++r) {
+            const int i = warp + NW * r;
+            const int gl = i / PER, ii = i - gl * PER;
+            const int h = CH == 32 ? (ii & 1) : 0, pair = CH == 32 ? (ii >> 1) : ii;
+            const int j = 16 * h + (lane >> 1);
+            const int plane = pair >> 3, mi = 2 * (pair & 7) + (lane & 1);
+            const int e = base + j;
+            const int l = e < n ? lidx[e] : 0;
+            stg[r] = gl < ng ? __ldg(a.shs + ((long long)(g0 + gl) * a.Lmax + l) * 32 + plane * 16 + mi)
+                             : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    auto store_rows = [&](const uint4 *stg, int s) {
+        unsigned char *st = stages + s * C::StageBytes;
+        constexpr int PER = CH;
+#pragma unroll
+        for (int r = 0; r < C::PIECES; ++r) {
+            const int i = warp + NW * r;
+            const int gl = i / PER, ii = i - gl * PER;
+            if (gl >= ng) continue;
+            const int h = CH == 32 ? (ii & 1) : 0, pair = CH == 32 ? (ii >> 1) : ii;
+            const int j = 16 * h + (lane >> 1);
+            const int plane = pair >> 3, mi = 2 * (pair & 7) + (lane & 1);
+            *reinterpret_cast<uint4 *>(st + gl * C::AGroup + plane * C::APlane + mi * (CH * 16) + j * 16) = stg[r];
+        }
+    };
     // split weights of listed samples [base, base + CH) into stage s (shared
     // by the groups): CH x 8 (sample, cell row) items of 8 cells, each done
     // by HV threads (8 / HV cells each)
@@ -345,8 +382,31 @@ __device__ __forceinline__ void grid_tc_item(const GridTcArgs &a, int g0, int ng
         const int nch = (n + CH - 1) / CH;
         if (nch == 0 || cta.failed) return;
         const int s0 = cta.stage;
-        const int npre = nch < P ? nch : P;
         bool bad = false;
+        if constexpr (C::REG) {
+            // chunk q: its rows (loaded last iteration) into stage q % NST once
+            // the MMAs of chunk q - NST are done, the next chunk's rows into
+            // registers, the weights, then the MMAs
+            uint4 stg[C::PIECES];
+            load_rows(stg, 0, n);
+            for (int q = 0; q < nch; ++q) {
+                const int s = (s0 + q) % NST;
+                if (!tc_stage_drain(cta, s)) bad = true;
+                if (!bad) store_rows(stg, s);
+                if (q + 1 < nch) load_rows(stg, (q + 1) * CH, n);
+                weights(s, q * CH, n);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                if (__syncthreads_or(bad)) { cta.failed = true; break; }
+                if (tid == 0) issue(s, first);
+                cta.pend |= 1u << s;
+                first = false;
+                ++issued;
+            }
+            cta.stage = (s0 + nch) % NST;
+            return;
+        }
+        const int npre = nch < P ? nch : P;
         for (int q = 0; q < npre; ++q) {
             const int s = (s0 + q) % NST;
             if (!tc_stage_drain(cta, s)) bad = true;

@@ -511,14 +511,11 @@ def test_tensor_core_zero_echo(dev):
 def test_tensor_core_gridding_is_deterministic(dev):
     """The same bits on every run, and for every pipeline variant with the
     same list capacity (the same listed order and the same chain of K = 16
-    steps per frequency group, only batched and scheduled differently:
-    variants 1-3 list 256 samples per pass, 4 lists 192); across capacities
-    the steps regroup at the pass boundaries and the images agree to FP32
-    rounding."""
+    steps per frequency group, only batched, staged and scheduled
+    differently)."""
     scan = synth.custom(**TC_CASES["many_tiles"])
     vols = {v: image_with(scan, dev, (2, 4, 0, v))[0] for v in (1, 2, 3, 4)}
     again = image_with(scan, dev, TC_FORM)[0]
     assert np.array_equal(again.view(np.uint64), vols[TC_FORM[3]].view(np.uint64))
-    assert np.array_equal(vols[1].view(np.uint64), vols[2].view(np.uint64))
-    assert np.array_equal(vols[1].view(np.uint64), vols[3].view(np.uint64))
-    assert rma.nmse(vols[1], vols[4]) <= TC_VS_FP32
+    for v in (1, 3, 4):
+        assert np.array_equal(vols[v].view(np.uint64), vols[2].view(np.uint64)), v
