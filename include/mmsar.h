@@ -136,16 +136,20 @@ typedef struct {
                                 * gridded together, the x weights applied once to *
                                 * their y-weighted sum (needs n_tx n_rx <= 16);   *
                                 * 0: sample by sample                              */
-    int grid_tensor_cores;     /* 1 .. 4: the gridding runs on the tensor cores as *
+    int grid_tensor_cores;     /* 1 .. 5: the gridding runs on the tensor cores as *
                                 * a per-tile product weights x samples, FP32-     *
                                 * accurate (FP16 hi/lo operands, FP32             *
                                 * accumulation); the value picks the pipeline:    *
-                                * 64-frequency groups per work item 4 (1, 2) or   *
-                                * 2 (3, 4); the sample rows staged through        *
+                                * 64-frequency groups per work item 4 (1, 2, 5)   *
+                                * or 2 (3, 4); the sample rows staged through     *
                                 * registers (1, 4) or by asynchronous copies with *
-                                * two (2) or four (3) shared-memory stages; all   *
-                                * give the same bits; the three fields above are  *
-                                * then ignored.  0: the FP32 FMA forms above      */
+                                * two (2) or four (3) shared-memory stages, all   *
+                                * giving the same bits; 5: one CTA per SM whose   *
+                                * warps list, gather, multiply and write back     *
+                                * concurrently (its own list segments: the same  *
+                                * sums to FP32 rounding, deterministic); the     *
+                                * three fields above are then ignored.  0: the    *
+                                * FP32 FMA forms above                             */
 } mmsar_tiles;
 
 /* Set (or read) the plan's gridding launch shape; the autotuner of the

@@ -122,6 +122,13 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
+// the same with the 128-byte swizzle (atoms of 8 K-rows x 128 bytes, 1024-byte
+// aligned): LBO = byte distance of MN-adjacent atoms, SBO = of K-adjacent
+// 8-row groups
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return tc_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -152,6 +159,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// the same without a compiler memory barrier: the copy's smem destination is
+// read only after cp.async.wait_group (which has one) and its global source is
+// not written by the kernel, so loads and address arithmetic of later copies
+// may be scheduled ahead of it
+__device__ __forceinline__ void cp_async16_free(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -679,6 +693,625 @@ __global__ void __launch_bounds__(C::T, C::MINB) grid_tc_multi(const __grid_cons
     tc_cta_end<C::NST, C::TmemCols>(cta, mbar);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form (grid_tensor_cores = 5).  One persistent CTA per SM
+// runs four roles concurrently, connected by mbarriers, so that listing the
+// next tile, gathering rows, the MMAs and the read-back of the previous
+// tile overlap instead of taking turns:
+//   warp 0       MMA issue (one thread): waits for a filled stage, issues the
+//                chunk's MMAs into the tile's accumulator, commits the stage
+//                back to the producers and, after a tile's last chunk, the
+//                accumulator to the epilogue;
+//   warps 1-4    list: the tile's candidate records in bin order, the kept
+//                samples and their Gaussian weights, into one of two list
+//                buffers (a tile with more than CAP samples fills several
+//                segments, accumulated into the same accumulator);
+//   warps 5-8    epilogue: accumulator (tcgen05.ld) x 2^-a_ref to G, then the
+//                accumulator is released to the MMA warp;
+//   warps 9-12   producers: per chunk of CH listed samples, the rows of every
+//                group of the item by cp.async (whole 128-byte lines) into a
+//                free stage and the split weights; a chunk is handed to the
+//                MMA warp P chunks later (once this thread's copies for it
+//                have landed and been made visible to the tensor cores).
+// Two accumulators of GB x 64 tensor-memory columns alternate between tiles.
+// The A operands (sample rows) use the 128-byte-swizzled MN-major layout,
+// the B operands (weights) the unswizzled one.  The chunking (CH consecutive
+// list entries, zero weights past the end of a segment) and the MMA order
+// are those of the forms above; the list segments differ (a round of
+// candidates is 128 records here), so the sums agree with them to rounding,
+// and the form is deterministic.
+// Every wait is bounded and also ends when another role has given up (a
+// shared abort flag); decisions the list warps take together go through a
+// barrier reduction, so no thread is left at a named barrier.
+constexpr int kWsListWarps = 4, kWsEpiWarps = 4, kWsProdWarps = 4;
+constexpr int kWsWarps = 1 + kWsListWarps + kWsEpiWarps + kWsProdWarps;
+constexpr int kWsT = 32 * kWsWarps;                       // 416 threads
+constexpr int kWsListT = 32 * kWsListWarps, kWsProdT = 32 * kWsProdWarps;
+constexpr int kWsListBar = 1;                             // named barrier of the list warps
+
+template <int NST_, int P_, int CAP_, int GB_>
+struct WsCfg {
+    static constexpr int CH = 16, NST = NST_, P = P_, CAP = CAP_, GB = GB_;
+    static_assert(P >= 1 && P < NST && NST <= 8, "stages");
+    static_assert(GB == 1 || GB == 2 || GB == 4, "groups per item");
+    static_assert(CAP >= kWsListT && CAP % CH == 0, "one round of candidates fits an empty list");
+    static constexpr int APlane = 16 * CH * 16;   // one plane (hi or lo) of one group: 2 MN atoms x 2 K groups
+    static constexpr int AGroup = 2 * APlane;
+    static constexpr int BPlane = 8 * CH * 16;
+    static constexpr int StageBytes = GB * AGroup + 2 * BPlane;
+    static_assert(StageBytes % 1024 == 0 && APlane % 1024 == 0, "swizzle atoms 1024-byte aligned");
+    static constexpr int ListBytes = CAP * 4 + 16 * CAP * 4;   // indices, weights [16][CAP]
+    static constexpr size_t Smem = (size_t)NST * StageBytes + 2 * (size_t)ListBytes + 1024;
+    static constexpr int AccCols = 64 * GB;                    // one accumulator
+    static constexpr int TmemCols = 2 * AccCols;               // two, alternating
+    static_assert((GB * CH) % kWsProdWarps == 0, "gather instructions split evenly over the producer warps");
+    static_assert(kWsProdT >= CH * 8, "one weight item per producer thread");
+};
+using WsCfg5 = WsCfg<4, 1, 256, 4>;
+
+template <int NST>
+struct WsShared {
+    unsigned long long full[NST], empty[NST];   // stage filled (producers), stage free (MMA commit)
+    unsigned long long lfull[2], lempty[2];     // list segment ready (list warps), consumed (producers)
+    unsigned long long afull[2], aempty[2];     // accumulator done (MMA commit), read (epilogue)
+    unsigned long long fin;                     // tear-down commit
+    int seg_n[2], seg_flags[2];                 // segment: entries; bit 0 first, bit 1 last of the tile
+    int st_flags[NST];                          // chunk of a stage: bit 0 first, bit 1 last, ng << 4
+    uint32_t tmem;
+    int abort;
+    int r_beg[kTcMaxRanges], r_pre[kTcMaxRanges + 1], slot_beg[kTcMaxRanges], slot_len[kTcMaxRanges];
+    int n_ranges;
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// Bounded wait that also returns (false) once another role has set the abort
+// flag; a wait that expires sets it.
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, volatile int *abort) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kTcWaitCycles) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+// The same for a whole (converged) warp: one lane waits, the others follow
+// it through the shuffle (a warp barrier); the result is warp-uniform.
+__device__ __forceinline__ bool ws_wait_warp(uint32_t mbar, uint32_t parity, volatile int *abort) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = ws_wait(mbar, parity, abort);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+// OR of a predicate over the threads of a named barrier (a barrier too; the
+// non-aligned forms, so a warp need not arrive converged)
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The work items of one scan (single launch) or of a table of scans (fused
+// batch), with the scan's arguments of an item.
+struct WsOneScan {
+    const GridTcArgs &a;
+    int gb;
+    __device__ int items() const { return (a.mrx >> 3) * (a.mry >> 3) * ((a.n_g + gb - 1) / gb); }
+    __device__ const GridTcArgs &args(int it, int &local) const {
+        local = it;
+        return a;
+    }
+    __device__ void mark_timeout() const { atomicOr(&a.hdr->error, kErrTimeout); }
+};
+struct WsTable {
+    const BatchTable<GridTcArgs> &t;
+    __device__ int items() const { return t.start[t.n]; }
+    __device__ const GridTcArgs &args(int it, int &local) const {
+        int lo = 0, hi = t.n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (t.start[mid] <= it) lo = mid; else hi = mid;
+        }
+        local = it - t.start[lo];
+        return t.a[lo];
+    }
+    __device__ void mark_timeout() const {
+        for (int i = 0; i < t.n; ++i) atomicOr(&t.a[i].hdr->error, kErrTimeout);
+    }
+};
+
+// An item's tile and group batch, and whether the tile is live (every role
+// walks the same item sequence and skips the same items).
+struct WsItem {
+    int tile, g0, ng;
+};
+template <class C>
+__device__ __forceinline__ bool ws_item(const GridTcArgs &a, int local, WsItem &w) {
+    const int n_tiles = (a.mrx >> 3) * (a.mry >> 3);
+    const int gb = local / n_tiles;
+    w.tile = local - gb * n_tiles;
+    w.g0 = gb * C::GB;
+    w.ng = min(C::GB, a.n_g - w.g0);
+    return tc_item_live(a, w.tile);
+}
+
+// List warps: the candidate records of each live item's tile, the kept
+// samples and their weights, one list segment (at most CAP entries) at a
+// time into list buffer (segments published) & 1.
+template <class C, class Src>
+__device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, unsigned char *lists) {
+    constexpr int CAP = C::CAP;
+    const int lt = threadIdx.x - 32, lwp = lt >> 5, lane = threadIdx.x & 31;
+    __shared__ int wc2[2][kWsListWarps];   // kept per warp, alternating between rounds
+    int sc = 0, rnd = 0;
+    // the next buffer is free once the producers have issued the segment it
+    // held two segments ago (one thread waits, the decision is shared)
+    auto acquire = [&]() -> bool {
+        bool bad = false;
+        if (sc >= 2 && lt == 0) bad = !ws_wait(smem_addr(&sh.lempty[sc & 1]), ((sc >> 1) - 1) & 1, &sh.abort);
+        return !bar_or(kWsListBar, kWsListT, bad);
+    };
+    auto publish = [&](int n, int flags) {
+        bar_named(kWsListBar, kWsListT);   // every entry of the segment written
+        if (lt == 0) {
+            sh.seg_n[sc & 1] = n;
+            sh.seg_flags[sc & 1] = flags;
+            mbar_arrive(smem_addr(&sh.lfull[sc & 1]));
+        }
+        ++sc;
+    };
+    const int items = src.items();
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        int local;
+        const GridTcArgs &a = src.args(it, local);
+        WsItem w;
+        if (!ws_item<C>(a, local, w)) continue;
+        // stop together once a wait here or in another CTA has expired
+        const bool give_up =
+            lt == 0 && (*reinterpret_cast<volatile int *>(&sh.abort) ||
+                        (*reinterpret_cast<volatile const int *>(&a.hdr->error) & kErrTimeout));
+        if (bar_or(kWsListBar, kWsListT, give_up)) {
+            if (lt == 0) sh.abort = 1;
+            break;
+        }
+        const int tiles_x = a.mrx >> 3;
+        const int U = (w.tile % tiles_x) * 8, V = (w.tile / tiles_x) * 8;
+        // candidate bins: first cells u0 in [U - (w - 1), U + 7], v0 likewise;
+        // per bin row one or two runs of consecutive bins (two where the run
+        // wraps around the periodic grid)
+        const int bu_lo = (U - (a.w - 1)) >> 2, bu_hi = (U + 7) >> 2;
+        const int bv_lo = (V - (a.w - 1)) >> 2, bv_hi = (V + 7) >> 2;
+        if (lt < kTcMaxRanges) {
+            const int rr = lt >> 1, part = lt & 1;
+            int beg = 0, len = 0;
+            if (bv_lo + rr <= bv_hi) {
+                const int row = (((bv_lo + rr) % a.nby) + a.nby) % a.nby;
+                const int s0 = ((bu_lo % a.nbx) + a.nbx) % a.nbx;
+                const int span = bu_hi - bu_lo + 1;
+                const int run0 = min(span, a.nbx - s0);
+                const int first = part == 0 ? s0 : 0, run = part == 0 ? run0 : span - run0;
+                if (run > 0) {
+                    beg = a.offsets[row * a.nbx + first];
+                    len = a.offsets[row * a.nbx + first + run] - beg;
+                }
+            }
+            sh.slot_beg[lt] = beg;
+            sh.slot_len[lt] = len;
+        }
+        bar_named(kWsListBar, kWsListT);
+        if (lt == 0) {
+            int n = 0, tot = 0;
+            for (int k = 0; k < kTcMaxRanges; ++k)
+                if (sh.slot_len[k] > 0) {
+                    sh.r_beg[n] = sh.slot_beg[k];
+                    sh.r_pre[n] = tot;
+                    tot += sh.slot_len[k];
+                    ++n;
+                }
+            sh.r_pre[n] = tot;
+            sh.n_ranges = n;
+        }
+        bar_named(kWsListBar, kWsListT);
+        const int n_ranges = sh.n_ranges, total = sh.r_pre[n_ranges];
+        const int a_ref = 127 - a.aref[0];
+        // the arguments used per candidate, in registers (the barriers are
+        // compiler memory barriers: a reference would be re-read after each)
+        const int mrx = a.mrx, mry = a.mry, kw = a.w;
+        const float kappa = a.kappa;
+        const int4 *const trec = a.trec;
+        const signed char *const sexp = a.sexp;
+        if (!acquire()) break;
+        int *lidx = reinterpret_cast<int *>(lists + (sc & 1) * C::ListBytes);
+        float *lw = reinterpret_cast<float *>(lidx + CAP);
+        auto record = [&](int c) {
+            if (c >= total) return make_int4(0, 0, 0, 0);
+            int k = 0;
+            while (k + 1 < n_ranges && sh.r_pre[k + 1] <= c) ++k;
+            return __ldg(trec + sh.r_beg[k] + (c - sh.r_pre[k]));
+        };
+        int n_list = 0, first = 1;
+        bool bad = false;
+        int4 rec_next = record(lt);
+        for (int base = 0; base < total; base += kWsListT) {
+            const int c = base + lt;
+            const int4 rec = rec_next;
+            rec_next = record(c + kWsListT);
+            bool keep = false;
+            int l = 0, du = 0, dv = 0;
+            float fx = 0.f, fy = 0.f;
+            if (c < total) {
+                l = rec.x;
+                du = (rec.y & 0xffff) - U;
+                dv = (rec.y >> 16) - V;
+                if (du < -(mrx >> 1)) du += mrx;
+                if (du >= (mrx >> 1)) du -= mrx;
+                if (dv < -(mry >> 1)) dv += mry;
+                if (dv >= (mry >> 1)) dv -= mry;
+                fx = __int_as_float(rec.z);
+                fy = __int_as_float(rec.w);
+                keep = du >= -(kw - 1) && du <= 7 && dv >= -(kw - 1) && dv <= 7;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            int *wc = wc2[rnd & 1];
+            ++rnd;
+            if (lane == 0) wc[lwp] = __popc(m);
+            bar_named(kWsListBar, kWsListT);
+            int before = 0, round = 0;
+#pragma unroll
+            for (int i = 0; i < kWsListWarps; ++i) {
+                before += i < lwp ? wc[i] : 0;
+                round += wc[i];
+            }
+            if (n_list + round > CAP) {   // (uniform) the segment is full: hand it over
+                publish(n_list, first);
+                first = 0;
+                n_list = 0;
+                if (!acquire()) {
+                    bad = true;
+                    break;
+                }
+                lidx = reinterpret_cast<int *>(lists + (sc & 1) * C::ListBytes);
+                lw = reinterpret_cast<float *>(lidx + CAP);
+            }
+            if (keep) {
+                const int e = n_list + before + __popc(m & ((1u << lane) - 1u));
+                lidx[e] = l;
+                // Gaussian weights exp(-kappa (f - tap)^2) on the tile's columns
+                // and rows (tap = cell - first cell, zero outside 0 .. w - 1),
+                // the rows with the factor 2^(a_ref - a) <= 1 (exact)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int tap = i - du;
+                    const float dlt = fx - (float)tap;
+                    lw[i * CAP + e] = (tap >= 0 && tap < kw) ? expf(-kappa * dlt * dlt) : 0.f;
+                }
+                const float scale = ldexpf(1.0f, a_ref - (int)sexp[l]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int tap = i - dv;
+                    const float dlt = fy - (float)tap;
+                    lw[(8 + i) * CAP + e] = (tap >= 0 && tap < kw) ? expf(-kappa * dlt * dlt) * scale : 0.f;
+                }
+            }
+            n_list += round;
+        }
+        if (bad) break;
+        publish(n_list, first | 2);
+    }
+    __syncwarp();
+}
+
+// Producer warps: per chunk of a segment, the rows of every group of the item
+// (cp.async) and the split weights into stage k % NST once the MMAs of chunk
+// k - NST are done; chunk k is handed to the MMA warp after chunk k + P is
+// issued (this thread's copies for it landed, then made visible to the
+// tensor cores), the rest at the end.
+template <class C, class Src>
+__device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages,
+                                              unsigned char *lists) {
+    constexpr int CH = C::CH, NST = C::NST, P = C::P, CAP = C::CAP, GB = C::GB;
+    const int pt = threadIdx.x - 32 * (1 + kWsListWarps + kWsEpiWarps), pw = pt >> 5, lane = threadIdx.x & 31;
+    const uint32_t st0 = smem_addr(stages);
+    int sc = 0, k = 0, kc = 0;   // segments consumed, chunks issued, chunks handed over
+    bool ok = true;
+    const int items = src.items();
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int local;
+        const GridTcArgs &a = src.args(it, local);
+        WsItem w;
+        if (!ws_item<C>(a, local, w)) continue;
+        // the item's row base in registers (not re-read through the argument reference)
+        const long long gstride = a.Lmax * 32;
+        const uint4 *const shs = a.shs + (long long)w.g0 * gstride;
+        bool last = false;
+        while (!last) {
+            const int b = sc & 1;
+            if (!ws_wait_warp(smem_addr(&sh.lfull[b]), (sc >> 1) & 1, &sh.abort)) {
+                ok = false;
+                break;
+            }
+            const int n = sh.seg_n[b], fl = sh.seg_flags[b];
+            last = (fl & 2) != 0;
+            const int *lidx = reinterpret_cast<const int *>(lists + b * C::ListBytes);
+            const float *lw = reinterpret_cast<const float *>(lidx + CAP);
+            const int nch = n > 0 ? (n + CH - 1) / CH : 1;   // an empty tile: one chunk of zero weights
+            for (int q = 0; q < nch; ++q) {
+                const int s = k % NST;
+                if (k >= NST && !ws_wait_warp(smem_addr(&sh.empty[s]), ((k / NST) - 1) & 1, &sh.abort)) {
+                    ok = false;
+                    break;
+                }
+                const int base = q * CH;
+                unsigned char *st = stages + s * C::StageBytes;
+                // rows: per group and plane the two 128-byte halves of each of
+                // the CH samples, one warp-instruction per 4 samples x 128
+                // bytes (whole lines); stored in the 128-byte-swizzled
+                // MN-major layout of the A operands: 16-byte chunk c of sample
+                // j's half h at h * 2048 + (j / 8) * 1024 + (j % 8) * 128 +
+                // (c ^ j % 8) * 16 (an atom is 8 samples x 64 halves)
+                constexpr int NR = GB * 16 / kWsProdWarps;
+                int lr[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {   // the listed samples first (independent loads)
+                    const int i = pw + kWsProdWarps * r;
+                    const int e = base + 4 * (i & 3) + (lane >> 3);
+                    lr[r] = e < n ? lidx[e] : 0;
+                }
+                const uint32_t sst = st0 + s * C::StageBytes;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int i = pw + kWsProdWarps * r;   // (group, plane, half, sample quad)
+                    const int gl = i >> 4, plane = (i >> 3) & 1, h = (i >> 2) & 1, sq = i & 3;
+                    if (gl >= w.ng) continue;
+                    const int j = 4 * sq + (lane >> 3), c = lane & 7;
+                    const uint4 *srcp = shs + gl * gstride + (long long)lr[r] * 32 + plane * 16 + 8 * h + c;
+                    cp_async16_free(sst + gl * C::AGroup + plane * C::APlane + h * 2048 + (j >> 3) * 1024 +
+                                        (j & 7) * 128 + ((c ^ (j & 7)) << 4),
+                                    srcp);
+                }
+                // split weights: one (sample, cell row) item of 8 cells per thread
+                if (pt < CH * 8) {
+                    const int j = pt % CH, rrow = pt / CH;
+                    const int e = base + j;
+                    float v[8];
+                    const float wy = e < n ? lw[(8 + rrow) * CAP + e] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = e < n ? lw[i * CAP + e] * wy : 0.f;
+                    uint4 hi, lo;
+                    split8(v, hi, lo);
+                    unsigned char *d = st + GB * C::AGroup + rrow * (CH * 16) + j * 16;
+                    *reinterpret_cast<uint4 *>(d) = hi;
+                    *reinterpret_cast<uint4 *>(d + C::BPlane) = lo;
+                }
+                if (pt == 0)
+                    sh.st_flags[s] = (((fl & 1) && q == 0) ? 1 : 0) | ((last && q == nch - 1) ? 2 : 0) | (w.ng << 4);
+                cp_async_commit();
+                ++k;
+                if (k - kc > P) {
+                    cp_async_wait<P>();
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(smem_addr(&sh.full[kc % NST]));
+                    ++kc;
+                }
+            }
+            if (!ok) break;
+            mbar_arrive(smem_addr(&sh.lempty[b]));   // the segment's entries are no longer read
+            ++sc;
+        }
+    }
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (ok)
+        for (; kc < k; ++kc) mbar_arrive(smem_addr(&sh.full[kc % NST]));
+    __syncwarp();
+}
+
+// MMA warp (one thread): per chunk, three MMAs per group into the item's
+// accumulator (the first chunk of a tile overwrites it), the stage committed
+// back to the producers; after a tile's last chunk the accumulator is
+// committed to the epilogue.  Accumulator t % 2 is reused by tile t once the
+// epilogue has read tile t - 2 from it.
+template <class C, class Src>
+__device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages) {
+    constexpr int NST = C::NST, GB = C::GB;
+    static_assert(C::CH == 16, "one K step per chunk");
+    // stage 0's operand descriptors: A with the 128-byte swizzle (MN atoms 2048
+    // bytes apart, 8-sample groups 1024 apart), B without (core matrices of 8
+    // samples x 16 bytes, K-adjacent 128 bytes apart, MN-adjacent 256)
+    const uint64_t da0 = tc_desc_sw128(smem_addr(stages), 2048, 1024);
+    const uint64_t db0 = tc_desc(smem_addr(stages) + GB * C::AGroup, 128, C::CH * 16);
+    int k = 0, tcount = 0;
+    const int items = src.items();
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        int local;
+        const GridTcArgs &a = src.args(it, local);
+        WsItem w;
+        if (!ws_item<C>(a, local, w)) continue;
+        const int ab = tcount & 1;
+        if (tcount >= 2 && !ws_wait(smem_addr(&sh.aempty[ab]), ((tcount >> 1) - 1) & 1, &sh.abort)) break;
+        const uint32_t acc = sh.tmem + (uint32_t)(ab * C::AccCols);
+        bool ok = true, tile_done = false;
+        while (!tile_done) {
+            const int s = k % NST;
+            if (!ws_wait(smem_addr(&sh.full[s]), (k / NST) & 1, &sh.abort)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int fl = sh.st_flags[s], ng = fl >> 4;
+            // descriptors of this stage: those of stage 0 plus the byte offset / 16
+            // (the 14-bit address field cannot carry: shared addresses < 256 KB)
+            const uint64_t so = (uint64_t)((s * C::StageBytes) >> 4);
+            const uint64_t dbh = db0 + so, dbl = dbh + (C::BPlane >> 4);
+#pragma unroll
+            for (int gl = 0; gl < GB; ++gl) {
+                if (gl >= ng) break;
+                const uint64_t dah = da0 + so + (uint64_t)((gl * C::AGroup) >> 4), dal = dah + (C::APlane >> 4);
+                const uint32_t d = acc + 64u * gl;
+                tc_mma(d, dah, dbh, (fl & 1) ? 0u : 1u);
+                tc_mma(d, dah, dbl, 1u);
+                tc_mma(d, dal, dbh, 1u);
+            }
+            tc_commit(smem_addr(&sh.empty[s]));
+            ++k;
+            if (fl & 2) {
+                tc_commit(smem_addr(&sh.afull[ab]));
+                tile_done = true;
+            }
+        }
+        if (!ok) break;
+        ++tcount;
+    }
+    // every MMA issued has completed before the stages and tensor memory go
+    tc_commit(smem_addr(&sh.fin));
+    if (!mbar_wait_bounded(smem_addr(&sh.fin), 0)) sh.abort = 1;
+}
+
+// Epilogue warps: lane quarter warp % 4 of each accumulator, x 2^-a_ref, to G
+// (row m = 32 (warp % 4) + lane: frequency 64 g + m / 2, component m % 2;
+// column n: cell (U + n % 8, V + n / 8)).
+template <class C, class Src>
+__device__ __noinline__ void ws_epilogue_role(const Src &src, WsShared<C::NST> &sh) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, mrow = 32 * quarter + lane;
+    int tcount = 0;
+    const int items = src.items();
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        int local;
+        const GridTcArgs &a = src.args(it, local);
+        WsItem w;
+        if (!ws_item<C>(a, local, w)) continue;
+        const int ab = tcount & 1;
+        if (!ws_wait_warp(smem_addr(&sh.afull[ab]), (tcount >> 1) & 1, &sh.abort)) break;   // (warp-uniform)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int tiles_x = a.mrx >> 3;
+        const int U = (w.tile % tiles_x) * 8, V = (w.tile / tiles_x) * 8;
+        const float unscale = ldexpf(1.0f, -(127 - a.aref[0]));
+        const int mrx = a.mrx, n_kc = a.n_kc;
+        const long long plane_stride = (long long)a.mry * a.mrx * kKC;
+        float2 *const G = a.G;
+        const uint32_t tmem = sh.tmem;
+        for (int gl = 0; gl < w.ng; ++gl) {
+            const int f = 64 * (w.g0 + gl) + (mrow >> 1);
+            const int kc = f >> 5;
+            const bool live = kc < n_kc;
+            // cell (U, V) of this row's frequency plane; cell (U + col, V + row)
+            // is row x rstride + col x 64 floats further
+            float *const cell0 = live ? reinterpret_cast<float *>(G + (long long)kc * plane_stride) + 2 * (f & 31) +
+                                            (mrow & 1) + ((long long)V * mrx + U) * (2 * kKC)
+                                      : nullptr;
+            const long long rstride = (long long)mrx * (2 * kKC);
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) +
+                                       (uint32_t)(ab * C::AccCols + 64 * gl + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n\ttcgen05.wait::ld.sync.aligned;"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                if (live) {
+                    float *const row0 = cell0 + (c0 >> 3) * rstride;   // columns c0 .. c0 + 15: two cell rows
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        row0[(i >> 3) * rstride + (i & 7) * (2 * kKC)] = __uint_as_float(r[i]) * unscale;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&sh.aempty[ab]));
+        ++tcount;
+    }
+    __syncwarp();
+}
+
+template <class C, class Src>
+__device__ __forceinline__ void grid_ws_body(const Src &src, unsigned char *smem, WsShared<C::NST> &sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < C::NST; ++s) {
+            mbar_init(smem_addr(&sh.full[s]), kWsProdT);
+            mbar_init(smem_addr(&sh.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_addr(&sh.lfull[b]), 1);
+            mbar_init(smem_addr(&sh.lempty[b]), kWsProdT);
+            mbar_init(smem_addr(&sh.afull[b]), 1);
+            mbar_init(smem_addr(&sh.aempty[b]), kWsEpiWarps);
+        }
+        mbar_init(smem_addr(&sh.fin), 1);
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sh.tmem)),
+                     "r"(C::TmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    unsigned char *stages = smem, *lists = smem + C::NST * C::StageBytes;
+    if (warp == 0) {
+        if (lane == 0) ws_mma_role<C>(src, sh, stages);
+        __syncwarp();
+    } else if (warp <= kWsListWarps) {
+        ws_list_role<C>(src, sh, lists);
+    } else if (warp <= kWsListWarps + kWsEpiWarps) {
+        ws_epilogue_role<C>(src, sh);
+    } else {
+        ws_producer_role<C>(src, sh, stages, lists);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && *reinterpret_cast<volatile int *>(&sh.abort)) src.mark_timeout();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sh.tmem), "r"(C::TmemCols));
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(kWsT, 1) grid_ws_kernel(const __grid_constant__ GridTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) WsShared<C::NST> sh;
+    grid_ws_body<C>(WsOneScan{a, C::GB}, smem, sh);
+}
+
+template <class C>
+__global__ void __launch_bounds__(kWsT, 1) grid_ws_multi(const __grid_constant__ BatchTable<GridTcArgs> t) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) WsShared<C::NST> sh;
+    grid_ws_body<C>(WsTable{t}, smem, sh);
+}
+
 static int grid_tc_describe(const Plan &p, void *ws, GridTcArgs &a) {
     char *w = reinterpret_cast<char *>(ws);
     a.shs = reinterpret_cast<const uint4 *>(w + p.off_shat);
@@ -731,8 +1364,24 @@ static cudaError_t grid_tc_launch(const GridTcArgs *a, const BatchTable<GridTcAr
     return cudaGetLastError();
 }
 
+template <class C>
+static cudaError_t grid_ws_launch(const GridTcArgs *a, const BatchTable<GridTcArgs> *t, int items, cudaStream_t s) {
+    // one CTA per SM (its shared memory and tensor memory take the SM)
+    if (a) {
+        cudaError_t e = ensure_smem_attr((const void *)grid_ws_kernel<C>, C::Smem);
+        if (e != cudaSuccess) return e;
+        grid_ws_kernel<C><<<tc_persistent_ctas(items, 1), kWsT, C::Smem, s>>>(*a);
+    } else {
+        cudaError_t e = ensure_smem_attr((const void *)grid_ws_multi<C>, C::Smem);
+        if (e != cudaSuccess) return e;
+        grid_ws_multi<C><<<tc_persistent_ctas(items, 1), kWsT, C::Smem, s>>>(*t);
+    }
+    return cudaGetLastError();
+}
+
 static int tc_variant_gb(int variant) {
     switch (variant) {
+        case 5: return WsCfg5::GB;
         case 1: return TcCfg1::GB;
         case 3: return TcCfg3::GB;
         case 4: return TcCfg4::GB;
@@ -743,6 +1392,7 @@ static int tc_variant_gb(int variant) {
 static cudaError_t grid_tc_dispatch(int variant, const GridTcArgs *a, const BatchTable<GridTcArgs> *t, int items,
                                     cudaStream_t s) {
     switch (variant) {
+        case 5: return grid_ws_launch<WsCfg5>(a, t, items, s);
         case 1: return grid_tc_launch<TcCfg1>(a, t, items, s);
         case 3: return grid_tc_launch<TcCfg3>(a, t, items, s);
         case 4: return grid_tc_launch<TcCfg4>(a, t, items, s);

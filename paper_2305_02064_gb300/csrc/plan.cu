@@ -166,7 +166,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.spread_nf = 2;
     p.spread_warps = 4;   // the autotuner's choice on the realistic, large and most batched scans
     p.grouped = false;
-    p.tc = 0;             // FP32 FMA gridding (the tensor-core variants 1..4 are autotuner options)
+    p.tc = 0;             // FP32 FMA gridding (the tensor-core variants 1..5 are autotuner options)
     p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;
@@ -287,8 +287,8 @@ mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
         return fail(MMSAR_ERR_INVALID_ARG, "the grouped form takes 1 or 2 frequencies per lane");
     if (tiles->grid_grouped && (int64_t)plan->p.shape.n_tx * plan->p.shape.n_rx > kMaxPairsGrouped)
         return fail(MMSAR_ERR_UNSUPPORTED_SIZE, "grouped gridding takes at most %d Tx/Rx pairs", kMaxPairsGrouped);
-    if (tiles->grid_tensor_cores < 0 || tiles->grid_tensor_cores > 4)
-        return fail(MMSAR_ERR_INVALID_ARG, "grid_tensor_cores must be 0 .. 4");
+    if (tiles->grid_tensor_cores < 0 || tiles->grid_tensor_cores > 5)
+        return fail(MMSAR_ERR_INVALID_ARG, "grid_tensor_cores must be 0 .. 5");
     plan->p.spread_nf = tiles->grid_freqs_per_lane;
     plan->p.spread_warps = tiles->grid_warps_per_cta;
     plan->p.grouped = tiles->grid_grouped != 0;

@@ -16,7 +16,7 @@ from __future__ import annotations
 # (frequencies per lane, warps per CTA, grouped, tensor cores): the
 # tensor-core form, then the FP32 forms (four frequencies per lane: 4 x 2-cell
 # warp blocks, per-sample form only)
-TENSOR_CORES = tuple((2, 4, 0, v) for v in (2, 1, 3, 4))   # the pipeline variants
+TENSOR_CORES = tuple((2, 4, 0, v) for v in (5, 2, 1, 3, 4))   # the pipeline variants
 SHAPES = (TENSOR_CORES + tuple((nf, wp, gr, 0) for gr in (1, 0) for nf, wp in ((2, 8), (1, 8), (2, 4), (1, 4)))
           + ((4, 8, 0, 0), (4, 4, 0, 0)))
 

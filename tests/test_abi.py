@@ -109,12 +109,12 @@ def test_gridding_launch_shape_setter():
     for shp in ((1, 4, 0), (2, 4, 1), (4, 4, 0), (1, 8, 1), (4, 8, 0), (2, 8, 0)):
         p.set_tiles(*shp)
         assert p.tiles == shp + (0,)
-    for v in (1, 2, 3, 4):
+    for v in (1, 2, 3, 4, 5):
         p.set_tiles(2, 4, 0, v)
         assert p.tiles == (2, 4, 0, v)
     p.set_tiles(2, 8, 0)
     for bad in ((0, 8, 0), (3, 8, 0), (8, 4, 0), (4, 4, 1), (2, 2, 0), (2, 16, 0), (-1, 4, 0), (2, 8, 2),
-                (2, 4, 0, 5), (2, 4, 0, -1)):
+                (2, 4, 0, 6), (2, 4, 0, -1)):
         with pytest.raises(MmsarError, match="INVALID_ARG"):
             p.set_tiles(*bad)
     assert p.tiles == (2, 8, 0, 0)   # the last valid setting stays

@@ -57,7 +57,7 @@ def test_fused_batch_equals_single(dev):
     from paper_2305_02064_gb300.batch import ScanJob, image_batch_fused
     scans = small_mix(8)
     jobs = [ScanJob(s, dev, dtype="f16" if i % 3 == 2 else "c64") for i, s in enumerate(scans)]
-    shapes = [(2, 4, 0, 2), (1, 8, 0), (2, 8, 1), (4, 4, 0), (2, 4, 0, 3), (4, 8, 0)]
+    shapes = [(2, 4, 0, 2), (1, 8, 0), (2, 8, 1), (2, 4, 0, 5), (4, 4, 0), (2, 4, 0, 3), (4, 8, 0)]
     for i, j in enumerate(jobs):
         j.plan.set_tiles(*shapes[i % len(shapes)])
     single = []

@@ -42,7 +42,8 @@ def test_deepest_z_grids(dev, nz):
     assert_parity(got, exact(scan), plan.kernel_width)
 
 
-TC = (2, 4, 0, 2)   # tensor-core gridding
+TC = (2, 4, 0, 2)   # tensor-core gridding (staged)
+WS = (2, 4, 0, 5)   # tensor-core gridding (warp-specialised)
 
 
 def run_with(scan, dev, tiles=None, **plan_kw):
@@ -61,7 +62,7 @@ def run_with(scan, dev, tiles=None, **plan_kw):
     return vol.cpu().numpy(), plan
 
 
-@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
+@pytest.mark.parametrize("tiles", [None, TC, WS], ids=["fp32", "tc", "ws"])
 @pytest.mark.parametrize("nk", [1024, 1000, 1023])
 def test_largest_frequency_counts(dev, nk, tiles):
     """Nk at the limit (1024: sixteen 64-frequency groups), below it (1000,
@@ -80,7 +81,7 @@ def test_too_many_frequencies_are_refused(dev):
         Plan(1, 2, 16, 32, 77e9, 1e8, synth.centred_grid(16, 16, 257, 1e-3, 5e-3, 0.26))
 
 
-@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
+@pytest.mark.parametrize("tiles", [None, TC, WS], ids=["fp32", "tc", "ws"])
 def test_largest_spectral_grid_on_both_axes(dev, tiles):
     """Mx = My = 1024 (the plan's largest) on a small voxel grid: 2048-point
     FFTs along x' and y', 1024-point inverse FFTs along k_y and k_x, a
@@ -117,7 +118,7 @@ def multi_tile():
     return scan, rma.rma_fast(rma.setup_from(scan), w=16)
 
 
-@pytest.mark.parametrize("tiles", [None, TC], ids=["fp32", "tc"])
+@pytest.mark.parametrize("tiles", [None, TC, WS], ids=["fp32", "tc", "ws"])
 @pytest.mark.parametrize("tol,w", [(1e-4, 8), (1e-5, 10), (1e-6, 12)])
 def test_wide_kernels_on_many_tiles(dev, multi_tile, tol, w, tiles):
     scan, ref = multi_tile

@@ -404,13 +404,19 @@ def test_autotune_picks_a_shape_and_keeps_the_image(dev, tiny_scan):
 
 # ----------------------------------------------------------------------------- tensor-core gridding
 # The tensor-core gridding (FP16 hi/lo operands, FP32 accumulation; plan
-# option grid_tensor_cores = 1..4) against the FP32 FMA form that the tests
+# option grid_tensor_cores = 1..5) against the FP32 FMA form that the tests
 # above exercise, and against the oracle.  The two compute the same sums to
 # FP32 rounding: NMSE between them <= 1e-10 (three transforms of ~2^-22
 # relative error per term give ~1e-13; the margin covers summation order).
 TC_FORM = (2, 4, 0, 2)
+WS_FORM = (2, 4, 0, 5)   # the warp-specialised kernel
 FP32_FORM = (2, 4, 0, 0)
 TC_VS_FP32 = 1e-10
+
+
+@pytest.fixture(params=[TC_FORM, WS_FORM], ids=["staged", "warp_specialised"])
+def tc_form(request):
+    return request.param
 
 
 def image_with(scan, dev, tiles, echo=None, dtype="c64", **plan_kw):
@@ -442,9 +448,9 @@ TC_CASES = {
 
 @pytest.mark.parametrize("case", sorted(TC_CASES))
 @pytest.mark.parametrize("plan_kw", [{}, {"nufft_tol": 1e-6}, {"compensate": 2}], ids=["w6", "w12", "mode2"])
-def test_tensor_core_gridding_matches_fp32_form(dev, case, plan_kw):
+def test_tensor_core_gridding_matches_fp32_form(dev, case, plan_kw, tc_form):
     scan = synth.custom(**TC_CASES[case])
-    tc, plan = image_with(scan, dev, TC_FORM, **plan_kw)
+    tc, plan = image_with(scan, dev, tc_form, **plan_kw)
     fp, _ = image_with(scan, dev, FP32_FORM, **plan_kw)
     assert np.all(np.isfinite(tc))
     assert rma.nmse(tc, fp) <= TC_VS_FP32, rma.nmse(tc, fp)
@@ -454,57 +460,57 @@ def test_tensor_core_gridding_matches_fp32_form(dev, case, plan_kw):
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
-def test_tensor_core_gridding_reduced_storage(dev, dtype):
+def test_tensor_core_gridding_reduced_storage(dev, dtype, tc_form):
     scan = synth.custom(**TC_CASES["many_tiles"])
-    tc, _ = image_with(scan, dev, TC_FORM, dtype=dtype)
+    tc, _ = image_with(scan, dev, tc_form, dtype=dtype)
     fp, _ = image_with(scan, dev, FP32_FORM, dtype=dtype)
     assert rma.nmse(tc, fp) <= TC_VS_FP32
 
 
-def test_tensor_core_dense_tiles(dev):
+def test_tensor_core_dense_tiles(dev, tc_form):
     """Positions at a quarter of the grid pitch: thousands of samples reach
     each 8 x 8-cell tile, so the per-tile list runs in several passes into
     the same accumulator."""
     scan = synth.custom(nx_pos=48, ny_pos=40, nk=24, layout="awr1443", nx=16, ny=16, nz=8, dx=4e-3, seed=17,
                         jitter=(0.3e-3, 1e-3), n_points=3)
-    tc, plan = image_with(scan, dev, TC_FORM)
+    tc, plan = image_with(scan, dev, tc_form)
     fp, _ = image_with(scan, dev, FP32_FORM)
     assert rma.nmse(tc, fp) <= TC_VS_FP32
     assert_parity(tc, oracle_of(scan), plan.kernel_width)
 
 
-def test_tensor_core_empty_tiles_inside_the_window(dev):
+def test_tensor_core_empty_tiles_inside_the_window(dev, tc_form):
     """Two clusters of positions far apart: the occupied window spans the gap,
     whose tiles list no sample and must come out zero."""
     a = synth.custom(nx_pos=6, ny_pos=5, nk=16, layout="awr1443", nx=64, ny=32, nz=8, seed=5, n_points=2)
     pos = np.concatenate([np.asarray(a.pos) + [-0.022, 0, 0], np.asarray(a.pos) + [0.022, 0, 0]])
     echo = synth.echo(pos, a.tx, a.rx, a.f0, a.df, 16, a.scatterers)
     scan = dataclasses.replace(a, pos=pos, echo=echo)
-    tc, plan = image_with(scan, dev, TC_FORM)
+    tc, plan = image_with(scan, dev, tc_form)
     fp, _ = image_with(scan, dev, FP32_FORM)
     assert rma.nmse(tc, fp) <= TC_VS_FP32
     assert_parity(tc, oracle_of(scan), plan.kernel_width)
 
 
-def test_tensor_core_extreme_magnitudes(dev):
+def test_tensor_core_extreme_magnitudes(dev, tc_form):
     """The per-row power-of-two normalisation keeps FP32 accuracy over the
     FP32 range: the image scales linearly from 1e-30 to 1e30, and samples of
     very different magnitudes in one scan still agree with the FP32 form."""
     scan = synth.custom(**TC_CASES["ragged"])
-    base, _ = image_with(scan, dev, TC_FORM)
+    base, _ = image_with(scan, dev, tc_form)
     for f in (1e-30, 1e30):
-        v, _ = image_with(scan, dev, TC_FORM, echo=(scan.echo * np.float32(f)).astype(np.complex64))
+        v, _ = image_with(scan, dev, tc_form, echo=(scan.echo * np.float32(f)).astype(np.complex64))
         assert rma.nmse(v / f, base) <= TC_VS_FP32, f
     mixed = scan.echo.copy()
     mixed[:, :, ::2] *= np.float32(1e6)
-    tc, _ = image_with(scan, dev, TC_FORM, echo=mixed)
+    tc, _ = image_with(scan, dev, tc_form, echo=mixed)
     fp, _ = image_with(scan, dev, FP32_FORM, echo=mixed)
     assert rma.nmse(tc, fp) <= TC_VS_FP32
 
 
-def test_tensor_core_zero_echo(dev):
+def test_tensor_core_zero_echo(dev, tc_form):
     scan = synth.custom(**TC_CASES["ragged"])
-    v, _ = image_with(scan, dev, TC_FORM, echo=np.zeros_like(scan.echo))
+    v, _ = image_with(scan, dev, tc_form, echo=np.zeros_like(scan.echo))
     assert np.all(v == 0)
 
 
@@ -519,3 +525,15 @@ def test_tensor_core_gridding_is_deterministic(dev):
     assert np.array_equal(again.view(np.uint64), vols[TC_FORM[3]].view(np.uint64))
     for v in (1, 3, 4):
         assert np.array_equal(vols[v].view(np.uint64), vols[2].view(np.uint64)), v
+
+
+def test_warp_specialised_gridding_is_deterministic(dev):
+    """The warp-specialised kernel lists in rounds of 128 candidates (256 in
+    the staged forms), so its list segments, and hence its chains of K = 16
+    steps, can differ from theirs: the same bits on every run, and the staged
+    forms' result to FP32 rounding."""
+    scan = synth.custom(**TC_CASES["many_tiles"])
+    a = image_with(scan, dev, WS_FORM)[0]
+    b = image_with(scan, dev, WS_FORM)[0]
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    assert rma.nmse(a, image_with(scan, dev, TC_FORM)[0]) <= TC_VS_FP32
