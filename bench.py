@@ -51,7 +51,7 @@ UNIT = "voxels/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["realistic", "tiny", "large", "batch", "serve", "psf"], default="realistic")
@@ -198,8 +198,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 20):
         self.gpu = gpu_index
+        self.period_ms = period_ms
         self.proc = None
         self.path = None
 
@@ -209,7 +210,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "100"], stdout=self.fh,
+                                          "-i", str(self.gpu), "-lms", str(self.period_ms)], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -240,7 +241,7 @@ class ClockSampler:
         inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
         window = "timed region"
         if not inside:
-            inside, window = rows, "whole run (timed region shorter than the 100 ms sampling period)"
+            inside, window = rows, f"whole run (timed region shorter than the {self.period_ms} ms sampling period)"
         reasons = set()
         for r in inside:
             active = r[3]
@@ -486,6 +487,22 @@ def run_ours(args, dist):
     plan.set_stage_events(None)
     clk = clocks.stop(w0, w1)
     plan.poll_error(ws, stream=stream)
+    # a sustained window after the timed region (not timed): about a second of
+    # the same steps with the clocks sampled, for runs whose timed region is
+    # short against the sampling period
+    sustained = ClockSampler(clocks.gpu)
+    sustained.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize(dev)
+    n_sus = max(1, int(1.0 / max(t_start.elapsed_time(t_end) / args.steps * 1e-3, 1e-6)))
+    s0 = time.time()
+    for _ in range(n_sus):
+        step()
+    torch.cuda.synchronize(dev)
+    s1 = time.time()
+    clk_sustained = sustained.stop(s0, s1)
+    if clk_sustained is not None:
+        clk_sustained["steps"] = n_sus
     ms = t_start.elapsed_time(t_end) / args.steps
     ms_max = dist.max(ms)
 
@@ -578,6 +595,7 @@ def run_ours(args, dist):
                 "serial_ms_per_step": e2e_serial_ms, "serial_value": total_vox / (e2e_serial_ms * 1e-3)},
         "gpu_launches": plan.kernels_per_image * args.steps,
         "clocks": clk,
+        "clocks_sustained": clk_sustained,
         "grid_launch_shape": {"tensor_cores": plan.tiles[3], "freqs_per_lane": plan.tiles[0],
                               "warps_per_cta": plan.tiles[1], "grouped": plan.tiles[2],
                               "autotuned_ms": None if tuned is None else

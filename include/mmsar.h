@@ -124,7 +124,8 @@ mmsar_status mmsar_plan_info(const mmsar_plan *plan, int *kernel_width, int *mx,
  * form (another summation order); they differ in speed, which depends on the
  * scan (small scans fill the GPU better with smaller CTAs; arrays whose Tx
  * and Rx lie on one line along y give large groups).  The tensor-core form
- * agrees with them to FP32 rounding.  Defaults: 2, 4, 0, 0. */
+ * agrees with them to FP32 rounding.  Defaults: 2, 4, 0, 5 (the
+ * warp-specialised tensor-core form; the first three fields then unused). */
 typedef struct {
     int grid_freqs_per_lane;   /* 1: a CTA covers 32 frequencies; 2: 64; 4: 128,   *
                                 * in 4 x 2-cell warp blocks (fewer taps outside   *

@@ -166,7 +166,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.spread_nf = 2;
     p.spread_warps = 4;   // the autotuner's choice on the realistic, large and most batched scans
     p.grouped = false;
-    p.tc = 0;             // FP32 FMA gridding (the tensor-core variants 1..5 are autotuner options)
+    p.tc = 5;             // warp-specialised tensor-core gridding (0: FP32 FMA; all are autotuner options)
     p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;

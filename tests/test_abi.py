@@ -101,11 +101,10 @@ def test_realistic_workspace_fits_hbm():
 def test_gridding_launch_shape_setter():
     """mmsar_plan_set_tiles accepts the gridding forms and launch shapes and
     rejects everything else (the grouped form takes 1 or 2 frequencies per
-    lane); the default is the FP32 form over 64 frequencies on 4 warps, per
-    sample."""
+    lane); the default is the warp-specialised tensor-core form (5)."""
     from paper_2305_02064_gb300._lib import MmsarError
     p = _plan()
-    assert p.tiles == (2, 4, 0, 0)
+    assert p.tiles == (2, 4, 0, 5)
     for shp in ((1, 4, 0), (2, 4, 1), (4, 4, 0), (1, 8, 1), (4, 8, 0), (2, 8, 0)):
         p.set_tiles(*shp)
         assert p.tiles == shp + (0,)
