@@ -698,17 +698,18 @@ __global__ void __launch_bounds__(C::T, C::MINB) grid_tc_multi(const __grid_cons
 // runs four roles concurrently, connected by mbarriers, so that listing the
 // next tile, gathering rows, the MMAs and the read-back of the previous
 // tile overlap instead of taking turns:
-//   warp 0       MMA issue (one thread): waits for a filled stage, issues the
-//                chunk's MMAs into the tile's accumulator, commits the stage
-//                back to the producers and, after a tile's last chunk, the
-//                accumulator to the epilogue;
-//   warps 1-4    list: the tile's candidate records in bin order, the kept
+//   warps 0-1    MMA issue (one thread each, alternate frequency groups):
+//                wait for a filled stage, issue the chunk's MMAs into the
+//                tile's accumulator, commit the stage back to the producers
+//                and, after a tile's last chunk, the accumulator to the
+//                epilogue;
+//   warps 2-5    list: the tile's candidate records in bin order, the kept
 //                samples and their Gaussian weights, into one of two list
 //                buffers (a tile with more than CAP samples fills several
 //                segments, accumulated into the same accumulator);
-//   warps 5-8    epilogue: accumulator (tcgen05.ld) x 2^-a_ref to G, then the
-//                accumulator is released to the MMA warp;
-//   warps 9-12   producers: per chunk of CH listed samples, the rows of every
+//   warps 6-9    epilogue: accumulator (tcgen05.ld) x 2^-a_ref to G, then the
+//                accumulator is released to the MMA warps;
+//   warps 10-13  producers: per chunk of CH listed samples, the rows of every
 //                group of the item by cp.async (whole 128-byte lines) into a
 //                free stage and the split weights; a chunk is handed to the
 //                MMA warp P chunks later (once this thread's copies for it
@@ -723,9 +724,9 @@ __global__ void __launch_bounds__(C::T, C::MINB) grid_tc_multi(const __grid_cons
 // Every wait is bounded and also ends when another role has given up (a
 // shared abort flag); decisions the list warps take together go through a
 // barrier reduction, so no thread is left at a named barrier.
-constexpr int kWsListWarps = 4, kWsEpiWarps = 4, kWsProdWarps = 4;
-constexpr int kWsWarps = 1 + kWsListWarps + kWsEpiWarps + kWsProdWarps;
-constexpr int kWsT = 32 * kWsWarps;                       // 416 threads
+constexpr int kWsMmaWarps = 2, kWsListWarps = 4, kWsEpiWarps = 4, kWsProdWarps = 4;
+constexpr int kWsWarps = kWsMmaWarps + kWsListWarps + kWsEpiWarps + kWsProdWarps;
+constexpr int kWsT = 32 * kWsWarps;                       // 448 threads
 constexpr int kWsListT = 32 * kWsListWarps, kWsProdT = 32 * kWsProdWarps;
 constexpr int kWsListBar = 1;                             // named barrier of the list warps
 
@@ -841,9 +842,13 @@ struct WsTable {
 };
 
 // An item's tile and group batch, and whether the tile is live (every role
-// walks the same item sequence and skips the same items).
+// walks the same item sequence and skips the same items).  The occupied
+// window of the item's scan is read once per scan (it does not change during
+// the kernel): most items of a persistent CTA lie outside it.
 struct WsItem {
     int tile, g0, ng;
+    const WsHeader *hdr = nullptr;   // the scan whose window is cached
+    int u_lo = 0, u_len = 0, v_lo = 0, v_len = 0;
 };
 template <class C>
 __device__ __forceinline__ bool ws_item(const GridTcArgs &a, int local, WsItem &w) {
@@ -852,7 +857,16 @@ __device__ __forceinline__ bool ws_item(const GridTcArgs &a, int local, WsItem &
     w.tile = local - gb * n_tiles;
     w.g0 = gb * C::GB;
     w.ng = min(C::GB, a.n_g - w.g0);
-    return tc_item_live(a, w.tile);
+    if (a.hdr != w.hdr) {
+        w.hdr = a.hdr;
+        w.u_lo = a.hdr->u_lo;
+        w.u_len = a.hdr->u_len;
+        w.v_lo = a.hdr->v_lo;
+        w.v_len = a.hdr->v_len;
+    }
+    const int tiles_x = a.mrx >> 3;
+    return tile_meets_tc((w.tile % tiles_x) * 8, 8, w.u_lo, w.u_len, a.mrx) &&
+           tile_meets_tc((w.tile / tiles_x) * 8, 8, w.v_lo, w.v_len, a.mry);
 }
 
 // List warps: the candidate records of each live item's tile, the kept
@@ -861,7 +875,7 @@ __device__ __forceinline__ bool ws_item(const GridTcArgs &a, int local, WsItem &
 template <class C, class Src>
 __device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, unsigned char *lists) {
     constexpr int CAP = C::CAP;
-    const int lt = threadIdx.x - 32, lwp = lt >> 5, lane = threadIdx.x & 31;
+    const int lt = threadIdx.x - 32 * kWsMmaWarps, lwp = lt >> 5, lane = threadIdx.x & 31;
     __shared__ int wc2[2][kWsListWarps];   // kept per warp, alternating between rounds
     int sc = 0, rnd = 0;
     // the next buffer is free once the producers have issued the segment it
@@ -881,10 +895,10 @@ __device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, 
         ++sc;
     };
     const int items = src.items();
+    WsItem w;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         int local;
         const GridTcArgs &a = src.args(it, local);
-        WsItem w;
         if (!ws_item<C>(a, local, w)) continue;
         // stop together once a wait here or in another CTA has expired
         const bool give_up =
@@ -1030,15 +1044,16 @@ template <class C, class Src>
 __device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages,
                                               unsigned char *lists) {
     constexpr int CH = C::CH, NST = C::NST, P = C::P, CAP = C::CAP, GB = C::GB;
-    const int pt = threadIdx.x - 32 * (1 + kWsListWarps + kWsEpiWarps), pw = pt >> 5, lane = threadIdx.x & 31;
+    const int pt = threadIdx.x - 32 * (kWsMmaWarps + kWsListWarps + kWsEpiWarps), pw = pt >> 5,
+              lane = threadIdx.x & 31;
     const uint32_t st0 = smem_addr(stages);
     int sc = 0, k = 0, kc = 0;   // segments consumed, chunks issued, chunks handed over
     bool ok = true;
     const int items = src.items();
+    WsItem w;
     for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
         int local;
         const GridTcArgs &a = src.args(it, local);
-        WsItem w;
         if (!ws_item<C>(a, local, w)) continue;
         // the item's row base in registers (not re-read through the argument reference)
         const long long gstride = a.Lmax * 32;
@@ -1126,13 +1141,15 @@ __device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &
     __syncwarp();
 }
 
-// MMA warp (one thread): per chunk, three MMAs per group into the item's
-// accumulator (the first chunk of a tile overwrites it), the stage committed
-// back to the producers; after a tile's last chunk the accumulator is
-// committed to the epilogue.  Accumulator t % 2 is reused by tile t once the
-// epilogue has read tile t - 2 from it.
+// MMA warps (one thread each; warp mw takes groups mw, mw + kWsMmaWarps, ...):
+// per chunk, three MMAs per group into the item's accumulator (the first
+// chunk of a tile overwrites it), the stage committed back to the producers;
+// after a tile's last chunk the accumulator is committed to the epilogue.
+// Accumulator t % 2 is reused by tile t once the epilogue has read tile t - 2
+// from it.  (Two issuing threads: an MMA instruction occupies its thread for
+// longer than the tensor pipe needs to execute it.)
 template <class C, class Src>
-__device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages) {
+__device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages, int mw) {
     constexpr int NST = C::NST, GB = C::GB;
     static_assert(C::CH == 16, "one K step per chunk");
     // stage 0's operand descriptors: A with the 128-byte swizzle (MN atoms 2048
@@ -1142,10 +1159,10 @@ __device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, u
     const uint64_t db0 = tc_desc(smem_addr(stages) + GB * C::AGroup, 128, C::CH * 16);
     int k = 0, tcount = 0;
     const int items = src.items();
+    WsItem w;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         int local;
         const GridTcArgs &a = src.args(it, local);
-        WsItem w;
         if (!ws_item<C>(a, local, w)) continue;
         const int ab = tcount & 1;
         if (tcount >= 2 && !ws_wait(smem_addr(&sh.aempty[ab]), ((tcount >> 1) - 1) & 1, &sh.abort)) break;
@@ -1164,7 +1181,7 @@ __device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, u
             const uint64_t so = (uint64_t)((s * C::StageBytes) >> 4);
             const uint64_t dbh = db0 + so, dbl = dbh + (C::BPlane >> 4);
 #pragma unroll
-            for (int gl = 0; gl < GB; ++gl) {
+            for (int gl = mw; gl < GB; gl += kWsMmaWarps) {
                 if (gl >= ng) break;
                 const uint64_t dah = da0 + so + (uint64_t)((gl * C::AGroup) >> 4), dal = dah + (C::APlane >> 4);
                 const uint32_t d = acc + 64u * gl;
@@ -1196,10 +1213,10 @@ __device__ __noinline__ void ws_epilogue_role(const Src &src, WsShared<C::NST> &
     const int quarter = warp & 3, mrow = 32 * quarter + lane;
     int tcount = 0;
     const int items = src.items();
+    WsItem w;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
         int local;
         const GridTcArgs &a = src.args(it, local);
-        WsItem w;
         if (!ws_item<C>(a, local, w)) continue;
         const int ab = tcount & 1;
         if (!ws_wait_warp(smem_addr(&sh.afull[ab]), (tcount >> 1) & 1, &sh.abort)) break;   // (warp-uniform)
@@ -1256,15 +1273,15 @@ __device__ __forceinline__ void grid_ws_body(const Src &src, unsigned char *smem
     if (tid == 0) {
         for (int s = 0; s < C::NST; ++s) {
             mbar_init(smem_addr(&sh.full[s]), kWsProdT);
-            mbar_init(smem_addr(&sh.empty[s]), 1);
+            mbar_init(smem_addr(&sh.empty[s]), kWsMmaWarps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_addr(&sh.lfull[b]), 1);
             mbar_init(smem_addr(&sh.lempty[b]), kWsProdT);
-            mbar_init(smem_addr(&sh.afull[b]), 1);
+            mbar_init(smem_addr(&sh.afull[b]), kWsMmaWarps);
             mbar_init(smem_addr(&sh.aempty[b]), kWsEpiWarps);
         }
-        mbar_init(smem_addr(&sh.fin), 1);
+        mbar_init(smem_addr(&sh.fin), kWsMmaWarps);
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1277,12 +1294,12 @@ __device__ __forceinline__ void grid_ws_body(const Src &src, unsigned char *smem
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     unsigned char *stages = smem, *lists = smem + C::NST * C::StageBytes;
-    if (warp == 0) {
-        if (lane == 0) ws_mma_role<C>(src, sh, stages);
+    if (warp < kWsMmaWarps) {
+        if (lane == 0) ws_mma_role<C>(src, sh, stages, warp);
         __syncwarp();
-    } else if (warp <= kWsListWarps) {
+    } else if (warp < kWsMmaWarps + kWsListWarps) {
         ws_list_role<C>(src, sh, lists);
-    } else if (warp <= kWsListWarps + kWsEpiWarps) {
+    } else if (warp < kWsMmaWarps + kWsListWarps + kWsEpiWarps) {
         ws_epilogue_role<C>(src, sh);
     } else {
         ws_producer_role<C>(src, sh, stages, lists);
