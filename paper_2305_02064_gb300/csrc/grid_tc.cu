@@ -709,11 +709,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) grid_tc_multi(const __grid_cons
 //                segments, accumulated into the same accumulator);
 //   warps 6-9    epilogue: accumulator (tcgen05.ld) x 2^-a_ref to G, then the
 //                accumulator is released to the MMA warps;
-//   warps 10-13  producers: per chunk of CH listed samples, the rows of every
-//                group of the item by cp.async (whole 128-byte lines) into a
-//                free stage and the split weights; a chunk is handed to the
-//                MMA warp P chunks later (once this thread's copies for it
-//                have landed and been made visible to the tensor cores).
+//   warps 10-13  producers: per chunk of CH listed samples, the split weights
+//                and the rows of every group of the item by cp.async (whole
+//                128-byte lines) into a free stage; each thread arrives on
+//                the stage's barrier once after its weight stores and once
+//                more, by the copy unit, when its copies have landed
+//                (cp.async.mbarrier.arrive.noinc), so a chunk is handed over
+//                as soon as its data is there; the MMA threads make the
+//                landed copies visible to the tensor cores with a proxy fence
+//                after their wait.
 // Two accumulators of GB x 64 tensor-memory columns alternate between tiles.
 // The A operands (sample rows) use the 128-byte-swizzled MN-major layout,
 // the B operands (weights) the unswizzled one.  The chunking (CH consecutive
@@ -730,10 +734,10 @@ constexpr int kWsT = 32 * kWsWarps;                       // 448 threads
 constexpr int kWsListT = 32 * kWsListWarps, kWsProdT = 32 * kWsProdWarps;
 constexpr int kWsListBar = 1;                             // named barrier of the list warps
 
-template <int NST_, int P_, int CAP_, int GB_>
+template <int NST_, int CAP_, int GB_>
 struct WsCfg {
-    static constexpr int CH = 16, NST = NST_, P = P_, CAP = CAP_, GB = GB_;
-    static_assert(P >= 1 && P < NST && NST <= 8, "stages");
+    static constexpr int CH = 16, NST = NST_, CAP = CAP_, GB = GB_;
+    static_assert(NST >= 2 && NST <= 8, "stages");
     static_assert(GB == 1 || GB == 2 || GB == 4, "groups per item");
     static_assert(CAP >= kWsListT && CAP % CH == 0, "one round of candidates fits an empty list");
     static constexpr int APlane = 16 * CH * 16;   // one plane (hi or lo) of one group: 2 MN atoms x 2 K groups
@@ -748,11 +752,11 @@ struct WsCfg {
     static_assert((GB * CH) % kWsProdWarps == 0, "gather instructions split evenly over the producer warps");
     static_assert(kWsProdT >= CH * 8, "one weight item per producer thread");
 };
-using WsCfg5 = WsCfg<4, 1, 256, 4>;
+using WsCfg5 = WsCfg<4, 256, 4>;
 
 template <int NST>
 struct WsShared {
-    unsigned long long full[NST], empty[NST];   // stage filled (producers), stage free (MMA commit)
+    unsigned long long full[NST], empty[NST];   // stage filled (producers: weights, then copies), free (MMA commits)
     unsigned long long lfull[2], lempty[2];     // list segment ready (list warps), consumed (producers)
     unsigned long long afull[2], aempty[2];     // accumulator done (MMA commit), read (epilogue)
     unsigned long long fin;                     // tear-down commit
@@ -769,6 +773,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, int count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// arrive on the barrier once every cp.async this thread has issued so far has
+// completed (the barrier's expected count includes this arrival)
+__device__ __forceinline__ void mbar_arrive_on_copies(uint32_t mbar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
 }
 // Bounded wait that also returns (false) once another role has set the abort
 // flag; a wait that expires sets it.
@@ -1035,19 +1044,19 @@ __device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, 
     __syncwarp();
 }
 
-// Producer warps: per chunk of a segment, the rows of every group of the item
-// (cp.async) and the split weights into stage k % NST once the MMAs of chunk
-// k - NST are done; chunk k is handed to the MMA warp after chunk k + P is
-// issued (this thread's copies for it landed, then made visible to the
-// tensor cores), the rest at the end.
+// Producer warps: per chunk of a segment, the split weights and the rows of
+// every group of the item (cp.async) into stage k % NST once the MMAs of
+// chunk k - NST are done; the stage's barrier completes when every producer
+// thread has arrived after its weight stores (with a proxy fence: the tensor
+// cores read them) and the copy unit has arrived for each thread's copies.
 template <class C, class Src>
 __device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &sh, unsigned char *stages,
                                               unsigned char *lists) {
-    constexpr int CH = C::CH, NST = C::NST, P = C::P, CAP = C::CAP, GB = C::GB;
+    constexpr int CH = C::CH, NST = C::NST, CAP = C::CAP, GB = C::GB;
     const int pt = threadIdx.x - 32 * (kWsMmaWarps + kWsListWarps + kWsEpiWarps), pw = pt >> 5,
               lane = threadIdx.x & 31;
     const uint32_t st0 = smem_addr(stages);
-    int sc = 0, k = 0, kc = 0;   // segments consumed, chunks issued, chunks handed over
+    int sc = 0, k = 0;   // segments consumed, chunks issued
     bool ok = true;
     const int items = src.items();
     WsItem w;
@@ -1078,6 +1087,25 @@ __device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &
                 }
                 const int base = q * CH;
                 unsigned char *st = stages + s * C::StageBytes;
+                // split weights: one (sample, cell row) item of 8 cells per thread
+                if (pt < CH * 8) {
+                    const int j = pt % CH, rrow = pt / CH;
+                    const int e = base + j;
+                    float v[8];
+                    const float wy = e < n ? lw[(8 + rrow) * CAP + e] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = e < n ? lw[i * CAP + e] * wy : 0.f;
+                    uint4 hi, lo;
+                    split8(v, hi, lo);
+                    unsigned char *d = st + GB * C::AGroup + rrow * (CH * 16) + j * 16;
+                    *reinterpret_cast<uint4 *>(d) = hi;
+                    *reinterpret_cast<uint4 *>(d + C::BPlane) = lo;
+                }
+                if (pt == 0)
+                    sh.st_flags[s] = (((fl & 1) && q == 0) ? 1 : 0) | ((last && q == nch - 1) ? 2 : 0) | (w.ng << 4);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_addr(&sh.full[s]));   // weights and chunk flags written
+
                 // rows: per group and plane the two 128-byte halves of each of
                 // the CH samples, one warp-instruction per 4 samples x 128
                 // bytes (whole lines); stored in the 128-byte-swizzled
@@ -1104,40 +1132,15 @@ __device__ __noinline__ void ws_producer_role(const Src &src, WsShared<C::NST> &
                                         (j & 7) * 128 + ((c ^ (j & 7)) << 4),
                                     srcp);
                 }
-                // split weights: one (sample, cell row) item of 8 cells per thread
-                if (pt < CH * 8) {
-                    const int j = pt % CH, rrow = pt / CH;
-                    const int e = base + j;
-                    float v[8];
-                    const float wy = e < n ? lw[(8 + rrow) * CAP + e] : 0.f;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v[i] = e < n ? lw[i * CAP + e] * wy : 0.f;
-                    uint4 hi, lo;
-                    split8(v, hi, lo);
-                    unsigned char *d = st + GB * C::AGroup + rrow * (CH * 16) + j * 16;
-                    *reinterpret_cast<uint4 *>(d) = hi;
-                    *reinterpret_cast<uint4 *>(d + C::BPlane) = lo;
-                }
-                if (pt == 0)
-                    sh.st_flags[s] = (((fl & 1) && q == 0) ? 1 : 0) | ((last && q == nch - 1) ? 2 : 0) | (w.ng << 4);
-                cp_async_commit();
+                mbar_arrive_on_copies(smem_addr(&sh.full[s]));   // the copies, once landed
                 ++k;
-                if (k - kc > P) {
-                    cp_async_wait<P>();
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_arrive(smem_addr(&sh.full[kc % NST]));
-                    ++kc;
-                }
             }
             if (!ok) break;
             mbar_arrive(smem_addr(&sh.lempty[b]));   // the segment's entries are no longer read
             ++sc;
         }
     }
-    cp_async_wait<0>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ok)
-        for (; kc < k; ++kc) mbar_arrive(smem_addr(&sh.full[kc % NST]));
+    asm volatile("cp.async.wait_all;" ::: "memory");   // no copy of this thread outlives the kernel
     __syncwarp();
 }
 
@@ -1174,6 +1177,9 @@ __device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, u
                 ok = false;
                 break;
             }
+            // the producers' copies landed through the generic proxy: make them
+            // visible to the tensor cores' (async proxy) reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int fl = sh.st_flags[s], ng = fl >> 4;
             // descriptors of this stage: those of stage 0 plus the byte offset / 16
@@ -1272,7 +1278,7 @@ __device__ __forceinline__ void grid_ws_body(const Src &src, unsigned char *smem
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < C::NST; ++s) {
-            mbar_init(smem_addr(&sh.full[s]), kWsProdT);
+            mbar_init(smem_addr(&sh.full[s]), 2 * kWsProdT);   // weights + copies per producer thread
             mbar_init(smem_addr(&sh.empty[s]), kWsMmaWarps);
         }
         for (int b = 0; b < 2; ++b) {
