@@ -160,6 +160,17 @@ typedef struct {
 mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles);
 mmsar_status mmsar_plan_get_tiles(const mmsar_plan *plan, mmsar_tiles *tiles);
 
+/* Test of the bounded device-side waits (no counterpart in the paper).  With
+ * on == 1, the next images of this plan run the warp-specialised tensor-core
+ * gridding (grid_tensor_cores = 5) with one MMA thread per CTA waiting on a
+ * barrier that nothing completes: the wait runs out after about half a
+ * second, the CTA's other warps stop at their next wait, every copy and MMA in
+ * flight is waited for and the tensor memory freed, and the error word gets
+ * MMSAR_ERR_DEVICE_TIMEOUT (mmsar_poll_error returns it; the image is void).
+ * The context stays usable: with on == 0 the next image is normal.  Other
+ * gridding forms ignore it.  INVALID_ARG for other values. */
+mmsar_status mmsar_plan_set_wait_test(mmsar_plan *plan, int on);
+
 /* Stages of mmsar_image, in launch order: 0 "prep" (reference plane,
  * geometry of Eq. 3-4 and 12, binning), 1 "compensate" (Eq. 11),
  * 2 "grid" (Gaussian gridding), 3 "fft_x", 4 "fft_y" (FT_2D of Eq. 16 with

@@ -91,10 +91,15 @@ class Plan:
 
     def set_tiles(self, freqs_per_lane: int, warps_per_cta: int, grouped: int = 0, tensor_cores: int = 0):
         """Gridding form and launch shape (see mmsar_plan_set_tiles; tune.autotune
-        picks one): tensor_cores=1 selects the tensor-core gridding (the other
-        fields are then ignored), else the FP32 FMA form given by the others."""
+        picks one): tensor_cores=1..5 selects a tensor-core gridding (the other
+        fields are then ignored), 0 the FP32 FMA form given by the others."""
         _lib.check(self._lib.mmsar_plan_set_tiles(self._h, ctypes.byref(
             _lib.Tiles(int(freqs_per_lane), int(warps_per_cta), int(grouped), int(tensor_cores)))))
+
+    def set_wait_test(self, on: bool):
+        """Exercise the bounded-wait expiry of the tensor-core gridding on the
+        next images (see mmsar_plan_set_wait_test; tests only)."""
+        _lib.check(self._lib.mmsar_plan_set_wait_test(self._h, 1 if on else 0))
 
     @property
     def tiles(self):

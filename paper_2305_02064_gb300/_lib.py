@@ -28,7 +28,7 @@ EXPORTS = ["mmsar_options_default", "mmsar_plan_create", "mmsar_plan_workspace_b
            "mmsar_image", "mmsar_poll_error", "mmsar_peak_scratch_bytes", "mmsar_peak", "mmsar_last_error",
            "mmsar_plan_destroy", "mmsar_version", "mmsar_static_workspace_bytes", "mmsar_image_static",
            "mmsar_quantize_echo", "mmsar_image_batch", "mmsar_image_batch_fused", "mmsar_backproject",
-           "mmsar_plan_set_tiles", "mmsar_plan_get_tiles"]
+           "mmsar_plan_set_tiles", "mmsar_plan_get_tiles", "mmsar_plan_set_wait_test"]
 
 
 class MmsarError(RuntimeError):
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True):
         lib.mmsar_backproject.restype = ctypes.c_int
         lib.mmsar_plan_set_tiles.argtypes = [vp, ctypes.POINTER(Tiles)]
         lib.mmsar_plan_set_tiles.restype = ctypes.c_int
+        lib.mmsar_plan_set_wait_test.argtypes = [vp, ctypes.c_int]
+        lib.mmsar_plan_set_wait_test.restype = ctypes.c_int
         lib.mmsar_plan_get_tiles.argtypes = [vp, ctypes.POINTER(Tiles)]
         lib.mmsar_plan_get_tiles.restype = ctypes.c_int
         lib.mmsar_version.argtypes = []

@@ -63,6 +63,7 @@ struct GridTcArgs {
     long long Lmax;
     int mrx, mry, nbx, nby, w, n_kc, n_g;
     float kappa;
+    int wait_test;             // 1: one MMA thread waits on a barrier nothing completes (timeout test)
 };
 
 constexpr int kTcMaxRanges = 16;
@@ -760,6 +761,7 @@ struct WsShared {
     unsigned long long lfull[2], lempty[2];     // list segment ready (list warps), consumed (producers)
     unsigned long long afull[2], aempty[2];     // accumulator done (MMA commit), read (epilogue)
     unsigned long long fin;                     // tear-down commit
+    unsigned long long never;                   // completed by nobody (the timeout test waits on it)
     int seg_n[2], seg_flags[2];                 // segment: entries; bit 0 first, bit 1 last of the tile
     int st_flags[NST];                          // chunk of a stage: bit 0 first, bit 1 last, ng << 4
     uint32_t tmem;
@@ -1168,6 +1170,8 @@ __device__ __noinline__ void ws_mma_role(const Src &src, WsShared<C::NST> &sh, u
         const GridTcArgs &a = src.args(it, local);
         if (!ws_item<C>(a, local, w)) continue;
         const int ab = tcount & 1;
+        // the timeout test: a wait that runs out, as a lost arrival would make it
+        if (a.wait_test && mw == 0 && !ws_wait(smem_addr(&sh.never), 0, &sh.abort)) break;
         if (tcount >= 2 && !ws_wait(smem_addr(&sh.aempty[ab]), ((tcount >> 1) - 1) & 1, &sh.abort)) break;
         const uint32_t acc = sh.tmem + (uint32_t)(ab * C::AccCols);
         bool ok = true, tile_done = false;
@@ -1288,6 +1292,7 @@ __device__ __forceinline__ void grid_ws_body(const Src &src, unsigned char *smem
             mbar_init(smem_addr(&sh.aempty[b]), kWsEpiWarps);
         }
         mbar_init(smem_addr(&sh.fin), kWsMmaWarps);
+        mbar_init(smem_addr(&sh.never), 1);
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1353,6 +1358,7 @@ static int grid_tc_describe(const Plan &p, void *ws, GridTcArgs &a) {
     a.n_kc = p.n_kc;
     a.n_g = (p.n_kc + 1) / 2;
     a.kappa = (float)(1.5 * kPi / p.w);
+    a.wait_test = p.wait_test;
     return (p.mrx / 8) * (p.mry / 8);   // tiles
 }
 

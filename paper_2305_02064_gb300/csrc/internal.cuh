@@ -81,7 +81,8 @@ struct Plan {
     int spread_nf;      // gridding launch shape: frequencies per lane (1, 2 or 4)
     int spread_warps;   //   and warps per CTA (4: 8 x 8 cells, 8: 16 x 8 cells; half as tall for 4)
     bool grouped;       // gridding by groups of samples sharing x' (else per sample)
-    int tc;             // gridding on the tensor cores, pipeline variant 1..4 (grid_tc.cu); 0: the FP32 forms above
+    int tc;             // gridding on the tensor cores, pipeline variant 1..5 (grid_tc.cu); 0: the FP32 forms above
+    int wait_test;      // 1: the warp-specialised gridding's bounded-wait expiry is exercised (tests only)
     int64_t G;          // group slots: n_tx n_rx n_pos (every class may be a single pair)
     int64_t n_bins;
     bool zref_given;

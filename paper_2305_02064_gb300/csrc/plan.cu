@@ -167,6 +167,7 @@ static mmsar_status build_plan(Plan &p, const mmsar_shape &sh, const mmsar_grid 
     p.spread_warps = 4;   // the autotuner's choice on the realistic, large and most batched scans
     p.grouped = false;
     p.tc = 5;             // warp-specialised tensor-core gridding (0: FP32 FMA; all are autotuner options)
+    p.wait_test = 0;
     p.G = p.L;
     p.zref_given = std::isfinite(o.z_ref);
     p.z_ref = p.zref_given ? o.z_ref : 0.0;
@@ -293,6 +294,13 @@ mmsar_status mmsar_plan_set_tiles(mmsar_plan *plan, const mmsar_tiles *tiles) {
     plan->p.spread_warps = tiles->grid_warps_per_cta;
     plan->p.grouped = tiles->grid_grouped != 0;
     plan->p.tc = tiles->grid_tensor_cores;
+    return MMSAR_OK;
+}
+
+mmsar_status mmsar_plan_set_wait_test(mmsar_plan *plan, int on) {
+    if (!plan) return fail(MMSAR_ERR_INVALID_ARG, "null plan");
+    if (on != 0 && on != 1) return fail(MMSAR_ERR_INVALID_ARG, "on must be 0 or 1");
+    plan->p.wait_test = on;
     return MMSAR_OK;
 }
 
@@ -475,7 +483,8 @@ mmsar_status mmsar_poll_error(const void *workspace, void *stream) {
     }
     if (word & kErrNonfinite) return fail(MMSAR_ERR_NONFINITE, "non-finite value in the echo or the geometry");
     if (word & kErrTimeout)
-        return fail(MMSAR_ERR_DEVICE_TIMEOUT, "a bounded device-side wait for an asynchronous copy gave up");
+        return fail(MMSAR_ERR_DEVICE_TIMEOUT,
+                    "a bounded device-side wait of the tensor-core gridding gave up: the image is void");
     if (word & kErrGeometry)
         return fail(MMSAR_ERR_INVALID_ARG, "z_scene does not lie beyond the reference plane z_ref (Z_c <= 0)");
     if (word) return fail(MMSAR_ERR_CUDA, "device error word 0x%x", word);

@@ -117,3 +117,16 @@ def test_gridding_launch_shape_setter():
         with pytest.raises(MmsarError, match="INVALID_ARG"):
             p.set_tiles(*bad)
     assert p.tiles == (2, 8, 0, 0)   # the last valid setting stays
+
+
+def test_wait_test_switch():
+    """mmsar_plan_set_wait_test takes 0 or 1 (the GPU test of the timeout path
+    is in test_gpu_timeout.py)."""
+    from paper_2305_02064_gb300 import _lib
+    from paper_2305_02064_gb300._lib import MmsarError
+    p = _plan()
+    for on in (1, 0):
+        _lib.check(p._lib.mmsar_plan_set_wait_test(p._h, on))
+    for bad in (2, -1):
+        with pytest.raises(MmsarError, match="INVALID_ARG"):
+            _lib.check(p._lib.mmsar_plan_set_wait_test(p._h, bad))
