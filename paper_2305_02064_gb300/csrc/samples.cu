@@ -1016,6 +1016,104 @@ __device__ __forceinline__ void compensate_body(const PrepTailArgs &a, int bid) 
 // planes: s_hat[g][l] = (hi[128 halves], lo[128 halves]).  The exponents
 // go to sexp[l]; aref (one int) receives the max of 127 - a.  The second
 // pass re-reads the warp's echo rows, which the first pass left in cache.
+// One pass for scans of at most kSplitRegGroups frequency groups (Nk <= 256):
+// U samples at a time, the lane's echo values of every group held in
+// registers while the warp finds each sample's bound, then rotated, scaled
+// and stored (the arithmetic of the two-pass form below, the same bits).
+constexpr int kSplitRegGroups = 4, kSplitRegU = 2;
+
+template <int DT, bool VEC>
+__device__ __forceinline__ void compensate_split_regs(const PrepTailArgs &a, int g0, int n_g, float scale, bool &bad,
+                                                      int &amax) {
+    constexpr int U = kSplitRegU;
+    const int lane = threadIdx.x & 31;
+    const int Nk = a.Nk;
+#pragma unroll 1
+    for (int u0 = 0; u0 < kCompUnroll; u0 += U) {
+        uint2 ph[U];
+        float mc[U];
+        float2 v[U][kSplitRegGroups][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int l = g0 + u0 + u;
+            ph[u] = l < a.L ? __ldg(a.phase + l) : make_uint2(0u, 0u);
+            mc[u] = 0.f;
+#pragma unroll
+            for (int g = 0; g < kSplitRegGroups; ++g) {
+                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+                if (g < n_g && l < a.L) {
+                    if (VEC) {
+                        const int k0 = 64 * g + 2 * lane;
+                        if (k0 < Nk) load_echo2<DT>(a.echo, ((long long)l * Nk + k0) >> 1, scale, v0, v1);
+                    } else {
+                        const int k = 64 * g + lane;
+                        if (k < Nk) v0 = load_echo<DT>(a.echo, (long long)l * Nk + k, scale);
+                        if (k + 32 < Nk) v1 = load_echo<DT>(a.echo, (long long)l * Nk + k + 32, scale);
+                    }
+                }
+                v[u][g][0] = v0;
+                v[u][g][1] = v1;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int g = 0; g < kSplitRegGroups; ++g)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 t = v[u][g][h];
+                    bad |= !(isfinite(t.x) && isfinite(t.y));
+                    mc[u] = fmaxf(mc[u], fmaxf(fabsf(t.x), fabsf(t.y)));
+                }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) mc[u] = fmaxf(mc[u], __shfl_xor_sync(0xffffffffu, mc[u], off));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int l = g0 + u0 + u;
+            // every component of s_hat is at most |s| <= sqrt(2) max(|Re s|, |Im s|)
+            const int ex = norm_exponent(mc[u] * 1.4142144f);
+            const float sc = ldexpf(1.0f, ex);
+            if (l >= a.L) continue;
+            amax = max(amax, 127 - ex);
+#pragma unroll
+            for (int g = 0; g < kSplitRegGroups; ++g) {
+                if (g >= n_g) continue;
+                float2 o0 = make_float2(0.f, 0.f), o1 = o0;
+                if (VEC) {
+                    const int k0 = 64 * g + 2 * lane;
+                    if (k0 < Nk) {
+                        const uint32_t t0 = ph[u].x + (uint32_t)k0 * ph[u].y;   // exact mod 2^32
+                        o0 = rotate_turns(v[u][g][0], t0);
+                        o1 = rotate_turns(v[u][g][1], t0 + ph[u].y);
+                    }
+                } else {
+                    const int k = 64 * g + lane;
+                    if (k < Nk) o0 = rotate_turns(v[u][g][0], ph[u].x + (uint32_t)k * ph[u].y);
+                    if (k + 32 < Nk) o1 = rotate_turns(v[u][g][1], ph[u].x + (uint32_t)(k + 32) * ph[u].y);
+                }
+                __half2 h0, l0, h1, l1;
+                split2(o0.x, o0.y, sc, h0, l0);
+                split2(o1.x, o1.y, sc, h1, l1);
+                __half2 *row = reinterpret_cast<__half2 *>(a.shat) + ((long long)g * a.L + l) * 128;   // 512 B
+                if (VEC) {   // complex 2 lane, 2 lane + 1 -> halves 4 lane .. 4 lane + 3
+                    row[2 * lane] = h0;
+                    row[2 * lane + 1] = h1;
+                    row[64 + 2 * lane] = l0;
+                    row[64 + 2 * lane + 1] = l1;
+                } else {     // complex lane and 32 + lane
+                    row[lane] = h0;
+                    row[32 + lane] = h1;
+                    row[64 + lane] = l0;
+                    row[64 + 32 + lane] = l1;
+                }
+            }
+            if (lane == 0) a.sexp[l] = (signed char)ex;
+        }
+    }
+}
+
 template <int DT, bool VEC>
 __device__ __forceinline__ void compensate_split_body(const PrepTailArgs &a, int cblk) {
     __shared__ int amax_s[kPrepWarps];
@@ -1026,6 +1124,10 @@ __device__ __forceinline__ void compensate_split_body(const PrepTailArgs &a, int
     bool bad = false;
     int amax = 0;
     for (int g0 = (cblk * kPrepWarps + warp) * kCompUnroll; g0 < a.L; g0 += warps * kCompUnroll) {
+        if (n_g <= kSplitRegGroups) {   // one pass, the echo values kept in registers
+            compensate_split_regs<DT, VEC>(a, g0, n_g, scale, bad, amax);
+            continue;
+        }
         uint2 ph[kCompUnroll];
         float mc[kCompUnroll];   // largest |Re s|, |Im s| of each sample (this lane's frequencies, then the warp's)
 #pragma unroll
