@@ -976,11 +976,18 @@ __device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, 
         };
         int n_list = 0, first = 1;
         bool bad = false;
-        int4 rec_next = record(lt);
+        // records two rounds ahead, the samples' exponents one round ahead
+        // (the exponent load depends on the record: both latencies overlap
+        // the rounds instead of adding to them)
+        int4 rec_next = record(lt), rec_next2 = record(lt + kWsListT);
+        int ex_next = lt < total ? (int)sexp[rec_next.x] : 0;
         for (int base = 0; base < total; base += kWsListT) {
             const int c = base + lt;
             const int4 rec = rec_next;
-            rec_next = record(c + kWsListT);
+            const int ex_l = ex_next;
+            rec_next = rec_next2;
+            ex_next = c + kWsListT < total ? (int)sexp[rec_next.x] : 0;
+            rec_next2 = record(c + 2 * kWsListT);
             bool keep = false;
             int l = 0, du = 0, dv = 0;
             float fx = 0.f, fy = 0.f;
@@ -1030,7 +1037,7 @@ __device__ __noinline__ void ws_list_role(const Src &src, WsShared<C::NST> &sh, 
                     const float dlt = fx - (float)tap;
                     lw[i * CAP + e] = (tap >= 0 && tap < kw) ? expf(-kappa * dlt * dlt) : 0.f;
                 }
-                const float scale = ldexpf(1.0f, a_ref - (int)sexp[l]);
+                const float scale = ldexpf(1.0f, a_ref - ex_l);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int tap = i - dv;
