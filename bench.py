@@ -300,8 +300,8 @@ def stage_bytes(plan, scan):
     if plan.tiles[3]:
         # tensor-core form: s_hat as FP16 hi / lo planes (the same bytes as
         # complex64), a 16-byte record per sample (bin order) and one
-        # normalisation exponent byte per sample and 64-frequency group
-        rec = 16 + nkp // 64 + (1 if nkp % 64 else 0)
+        # normalisation exponent byte per sample
+        rec = 16 + 1
     else:
         rec = (2 * (plan.kernel_width + 3) + 1) * 16 + 8   # weight record + (in-bin offset, sample index)
     # prep: geometry records, phases, bin ids, permutation; compensate: echo
