@@ -120,3 +120,19 @@ def test_host_cpu_reports_a_model():
     model, cores = bench.host_cpu()
     assert isinstance(model, str) and model
     assert cores >= 1
+
+
+def test_reference_arm_samples_track_the_whole_scan():
+    """With a step budget below one whole image, the reference arm times a
+    smaller sample (fewer frequencies, then fewer positions) and scales it by
+    the measured whole / sample ratio: its value stays close to the
+    whole-image rate, and the line says what the sample was."""
+    import argparse
+    args = argparse.Namespace(workload="tiny", compensate=1, steps=6, warmup=1, ref_budget=0.001)
+    out = bench.run_reference(args, bench.Dist(want_cuda=False))
+    assert out["impl"] == "reference" and out["steps"] == 6
+    whole = out["whole_scan_seconds"]
+    assert "ratio" in out["cpu_baseline"]["sample"]
+    est = out["ms_per_step"] * 1e-3
+    assert 0.5 * whole < est < 2.0 * whole, (est, whole)
+    assert out["cpu_baseline"]["value"] == out["value"] == out["e2e"]["value"]
