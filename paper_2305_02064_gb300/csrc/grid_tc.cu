@@ -753,7 +753,7 @@ struct WsCfg {
     static_assert((GB * CH) % kWsProdWarps == 0, "gather instructions split evenly over the producer warps");
     static_assert(kWsProdT >= CH * 8, "one weight item per producer thread");
 };
-using WsCfg5 = WsCfg<4, 256, 4>;
+using WsCfg5 = WsCfg<4, 512, 4>;
 
 template <int NST>
 struct WsShared {
